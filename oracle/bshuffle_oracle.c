@@ -1,0 +1,418 @@
+/*
+ * Plain, sequential CPU oracle for the bijective shuffle of
+ * "Bandwidth-Optimal Random Shuffling for GPUs" (arXiv 2106.06161).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent checker of the
+ * CUDA library: only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline leg may build, load or call it.  It shares no
+ * source, header, table or constant generator with the CUDA path, and the
+ * CUDA path never calls it.
+ *
+ * Everything here is written for obviousness, not speed: one index at a
+ * time, in the order the paper states the algorithm.
+ *
+ * Readings of the paper taken here (each is also listed with its reason in
+ * the design notes of the repository):
+ *   R1  mulhilo is the full 64-bit product of the 64-bit constant M0 with
+ *       the zero-extended 32-bit left half, reduced mod 2^64, then split into
+ *       upper and lower 32-bit words (Sec. 3.2, Listing 1 and its caption).
+ *   R2  the power-of-two domain has k = max(ceil(log2 n), 4) bits: with fewer
+ *       than 4 bits the left half has at most one bit, the multiply is linear
+ *       over GF(2) and the cipher can only reach 2^k affine permutations
+ *       (Sec. 4 says "nearest power of two"; the 4-bit floor is the reading
+ *       under which the Sec. 5 chi-squared result at n = 5 is reachable).
+ *       The *_k entry points take k explicitly so the literal rule stays
+ *       testable.
+ *   R3  the round keys are the low 32 bits of successive SplitMix64 outputs
+ *       (Steele, Lea, Flood, OOPSLA 2014) started from the 64-bit seed; the
+ *       paper only says "key[i]" and never gives a seed-to-key schedule.
+ *   R4  an image b is kept when b < n and dropped when b >= n (Algorithm 1).
+ *   R5  output convention: slot j receives X[f(i_j)], where i_j is the j-th
+ *       domain index, in increasing order, whose image is kept (Algorithm 1
+ *       is a gather in i-order; the exclusive scan of the keep flags is the
+ *       running count used below).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Philox multiplier named in Listing 1 (Sec. 3.2), from Salmon et al. */
+static const uint64_t ORACLE_M0 = 0xD2B74407B1CE6E93ULL;
+/* Reading R2: smallest domain exponent. */
+static const uint32_t ORACLE_K_MIN = 4;
+/* SplitMix64 increment (golden-ratio gamma), Steele-Lea-Flood 2014. */
+static const uint64_t ORACLE_SPLITMIX_GAMMA = 0x9E3779B97F4A7C15ULL;
+
+/* ------------------------------------------------------------------ */
+/* Domain (Sec. 4, first paragraph; reading R2)                        */
+/* ------------------------------------------------------------------ */
+
+/* Smallest k with 2^k >= n, never below ORACLE_K_MIN.  n = 0 gives 0. */
+uint32_t oracle_domain_bits(uint64_t n)
+{
+    uint32_t k = 0;
+    if (n == 0)
+        return 0;
+    while (k < 64 && ((uint64_t)1 << k) < n)
+        k++;
+    if (k < ORACLE_K_MIN)
+        k = ORACLE_K_MIN;
+    return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* Round keys (reading R3)                                             */
+/* ------------------------------------------------------------------ */
+
+static uint64_t oracle_splitmix64_next(uint64_t *state)
+{
+    uint64_t z;
+    *state += ORACLE_SPLITMIX_GAMMA;
+    z = *state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void oracle_round_keys(uint64_t seed, uint32_t rounds, uint32_t *keys)
+{
+    uint64_t state = seed;
+    uint32_t r;
+    for (r = 0; r < rounds; r++)
+        keys[r] = (uint32_t)oracle_splitmix64_next(&state);
+}
+
+/* ------------------------------------------------------------------ */
+/* VariablePhilox bijection on [0, 2^k) (Sec. 3.2, Listing 1)          */
+/* ------------------------------------------------------------------ */
+
+static uint64_t oracle_mask(uint32_t bits)
+{
+    return bits >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << bits) - 1);
+}
+
+/*
+ * Forward cipher.  The k-bit value is split into a left half of floor(k/2)
+ * bits (state[0]) and a right half of ceil(k/2) bits (state[1]); each round
+ *   - multiplies M0 by the left half (64-bit product, reading R1),
+ *   - forms the new right half from the low product word shifted up by the
+ *     odd-bit count (R - L) with the top bit of the old right half moved in
+ *     underneath (the function G of Sec. 3.2 mixing the odd bit b),
+ *   - forms the new left half as (high product word) XOR key XOR (old right
+ *     half), masked to L bits (L' = F_k(L) xor R in Sec. 3.2),
+ * and the halves are joined back as left << R | right.
+ */
+uint64_t oracle_varphilox(uint64_t x, uint32_t k, const uint32_t *keys, uint32_t rounds)
+{
+    const uint32_t left_bits = k / 2;
+    const uint32_t right_bits = k - left_bits;
+    const uint64_t left_mask = oracle_mask(left_bits);
+    const uint64_t right_mask = oracle_mask(right_bits);
+    uint32_t state0 = (uint32_t)(x >> right_bits);
+    uint32_t state1 = (uint32_t)(x & right_mask);
+    uint32_t r;
+
+    for (r = 0; r < rounds; r++) {
+        uint64_t product = ORACLE_M0 * (uint64_t)state0;  /* mod 2^64 */
+        uint32_t hi = (uint32_t)(product >> 32);
+        uint32_t lo = (uint32_t)product;
+        lo = (uint32_t)(lo << (right_bits - left_bits)) | (uint32_t)(state1 >> left_bits);
+        state0 = (uint32_t)(((uint64_t)(hi ^ keys[r]) ^ state1) & left_mask);
+        state1 = (uint32_t)((uint64_t)lo & right_mask);
+    }
+    return ((uint64_t)state0 << right_bits) | (uint64_t)state1;
+}
+
+/* Multiplicative inverse of an odd a modulo 2^64 by Newton's iteration
+ * x <- x (2 - a x); a*a = 1 mod 8 gives 3 correct bits to start, and each
+ * step doubles them (3, 6, 12, 24, 48, 96). */
+static uint64_t oracle_inverse_mod_2_64(uint64_t a)
+{
+    uint64_t x = a;
+    int it;
+    for (it = 0; it < 5; it++)
+        x = x * (2 - a * x);
+    return x;
+}
+
+uint64_t oracle_m0_inverse(void)
+{
+    return oracle_inverse_mod_2_64(ORACLE_M0);
+}
+
+/*
+ * Inverse cipher, the inversion steps of Sec. 3.2 applied round by round in
+ * reverse key order:
+ *   (B_k(L), b) = G^-1(R', b')   -- the low bit of the new right half is the
+ *                                   old top bit b (odd k only); the bits
+ *                                   above it are the low L bits of M0 * L,
+ *   L = B_k^-1(B_k(L))           -- multiply by M0^-1 modulo 2^L,
+ *   R = F_k(L) xor L'            -- recompute the high product word.
+ */
+uint64_t oracle_varphilox_inverse(uint64_t y, uint32_t k, const uint32_t *keys, uint32_t rounds)
+{
+    const uint32_t left_bits = k / 2;
+    const uint32_t right_bits = k - left_bits;
+    const uint32_t odd = right_bits - left_bits;          /* 0 or 1 */
+    const uint64_t left_mask = oracle_mask(left_bits);
+    const uint64_t right_mask = oracle_mask(right_bits);
+    const uint64_t m0_inv = oracle_inverse_mod_2_64(ORACLE_M0);
+    uint64_t new_left = y >> right_bits;
+    uint64_t new_right = y & right_mask;
+    uint32_t r;
+
+    for (r = rounds; r-- > 0;) {
+        uint64_t b = odd ? (new_right & 1) : 0;
+        uint64_t b_of_left = odd ? (new_right >> 1) : new_right;   /* = M0*L mod 2^L */
+        uint64_t left = (b_of_left * m0_inv) & left_mask;
+        uint64_t product = ORACLE_M0 * left;
+        uint64_t hi = product >> 32;
+        uint64_t right_low = (new_left ^ hi ^ (uint64_t)keys[r]) & left_mask;
+        uint64_t right = right_low | (b << left_bits);
+        new_left = left;
+        new_right = right;
+    }
+    return (new_left << right_bits) | new_right;
+}
+
+void oracle_varphilox_array(const uint64_t *x, uint64_t *y, uint64_t count, uint32_t k,
+                            const uint32_t *keys, uint32_t rounds)
+{
+    uint64_t t;
+    for (t = 0; t < count; t++)
+        y[t] = oracle_varphilox(x[t], k, keys, rounds);
+}
+
+void oracle_varphilox_inverse_array(const uint64_t *y, uint64_t *x, uint64_t count, uint32_t k,
+                                    const uint32_t *keys, uint32_t rounds)
+{
+    uint64_t t;
+    for (t = 0; t < count; t++)
+        x[t] = oracle_varphilox_inverse(y[t], k, keys, rounds);
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1 (Sec. 4): evaluate, flag, exclusive scan, gather         */
+/* ------------------------------------------------------------------ */
+
+/*
+ * idx[j] = f(i_j) for the j-th kept domain index, i ascending over [0, 2^k).
+ * The running count `j` is the exclusive scan of the keep flags.  Returns the
+ * number of kept indices (n for a bijection on a domain with 2^k >= n).
+ */
+uint64_t oracle_indices_k(uint64_t *idx, uint64_t n, uint32_t k, uint64_t seed, uint32_t rounds)
+{
+    uint32_t keys[256];
+    uint64_t domain, i, j = 0;
+    if (n == 0 || rounds > 256 || k > 40)
+        return 0;
+    oracle_round_keys(seed, rounds, keys);
+    domain = (uint64_t)1 << k;
+    for (i = 0; i < domain; i++) {
+        uint64_t b = oracle_varphilox(i, k, keys, rounds);
+        int flag = (b < n) ? 1 : 0;
+        if (flag) {
+            if (j < n)
+                idx[j] = b;
+            j++;
+        }
+    }
+    return j;
+}
+
+uint64_t oracle_indices(uint64_t *idx, uint64_t n, uint64_t seed, uint32_t rounds)
+{
+    return oracle_indices_k(idx, n, oracle_domain_bits(n), seed, rounds);
+}
+
+/* Y[out_idx] = X[b] (Algorithm 1), elements of elem_bytes bytes.  Returns the
+ * number of elements written. */
+uint64_t oracle_permute_k(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint32_t k,
+                          uint64_t seed, uint32_t rounds)
+{
+    const unsigned char *x = (const unsigned char *)in;
+    unsigned char *y = (unsigned char *)out;
+    uint32_t keys[256];
+    uint64_t domain, i, out_idx = 0;
+    if (n == 0 || rounds > 256 || k > 40)
+        return 0;
+    oracle_round_keys(seed, rounds, keys);
+    domain = (uint64_t)1 << k;
+    for (i = 0; i < domain; i++) {
+        uint64_t b = oracle_varphilox(i, k, keys, rounds);
+        if (b < n) {
+            memcpy(y + out_idx * elem_bytes, x + b * elem_bytes, elem_bytes);
+            out_idx++;
+        }
+    }
+    return out_idx;
+}
+
+uint64_t oracle_permute(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                        uint32_t rounds)
+{
+    return oracle_permute_k(in, out, n, elem_bytes, oracle_domain_bits(n), seed, rounds);
+}
+
+/* The inverse shuffle: out[f(i_j)] = in[j], so that inverse(permute(x)) = x. */
+uint64_t oracle_inverse(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                        uint32_t rounds)
+{
+    const unsigned char *x = (const unsigned char *)in;
+    unsigned char *y = (unsigned char *)out;
+    uint32_t keys[256];
+    uint32_t k = oracle_domain_bits(n);
+    uint64_t domain, i, j = 0;
+    if (n == 0 || rounds > 256 || k > 40)
+        return 0;
+    oracle_round_keys(seed, rounds, keys);
+    domain = (uint64_t)1 << k;
+    for (i = 0; i < domain; i++) {
+        uint64_t b = oracle_varphilox(i, k, keys, rounds);
+        if (b < n) {
+            memcpy(y + b * elem_bytes, x + j * elem_bytes, elem_bytes);
+            j++;
+        }
+    }
+    return j;
+}
+
+/* count permutations of length n (as idx arrays, uint32) from seeds
+ * seed0, seed0+1, ...; used by the statistical tests of Sec. 5. */
+void oracle_sample_permutations(uint32_t *perms, uint32_t n, uint64_t seed0, uint64_t count,
+                                uint32_t rounds)
+{
+    uint64_t s, j;
+    uint64_t *idx = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+    for (s = 0; s < count; s++) {
+        oracle_indices(idx, n, seed0 + s, rounds);
+        for (j = 0; j < n; j++)
+            perms[s * n + j] = (uint32_t)idx[j];
+    }
+    free(idx);
+}
+
+/* ------------------------------------------------------------------ */
+/* Fisher-Yates (Sec. 1): the sequential baseline, timing only          */
+/* ------------------------------------------------------------------ */
+
+/* Durstenfeld's in-place form; bounded integers by rejection from a
+ * SplitMix64 stream (no modulo bias). */
+void oracle_fisher_yates(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed)
+{
+    unsigned char *a = (unsigned char *)data;
+    unsigned char tmp[256];
+    uint64_t state = seed, i;
+    if (n < 2 || elem_bytes > sizeof(tmp))
+        return;
+    for (i = n - 1; i > 0; i--) {
+        uint64_t bound = i + 1;
+        uint64_t limit = ~(uint64_t)0 - (~(uint64_t)0 % bound);
+        uint64_t r, j;
+        do {
+            r = oracle_splitmix64_next(&state);
+        } while (r >= limit);
+        j = r % bound;
+        memcpy(tmp, a + i * elem_bytes, elem_bytes);
+        memcpy(a + i * elem_bytes, a + j * elem_bytes, elem_bytes);
+        memcpy(a + j * elem_bytes, tmp, elem_bytes);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Permutation Monte Carlo test statistic (application named in Sec. 1) */
+/* ------------------------------------------------------------------ */
+
+/*
+ * For each b < count: shuffle x (length n) with seed base_seed + b and
+ * return T_b = mean(y[0:n1]) - mean(y[n1:n]), summed in FP64 in slot order.
+ */
+void oracle_mc_statistics(const float *x, uint64_t n, uint64_t n1, uint64_t base_seed,
+                          uint64_t count, uint32_t rounds, double *T)
+{
+    uint32_t keys[256];
+    uint32_t k = oracle_domain_bits(n);
+    uint64_t domain = (uint64_t)1 << k;
+    uint64_t b, i;
+    if (n == 0 || n1 == 0 || n1 >= n || rounds > 256)
+        return;
+    for (b = 0; b < count; b++) {
+        double sum1 = 0.0, sum2 = 0.0;
+        uint64_t slot = 0;
+        oracle_round_keys(base_seed + b, rounds, keys);
+        for (i = 0; i < domain; i++) {
+            uint64_t src = oracle_varphilox(i, k, keys, rounds);
+            if (src < n) {
+                if (slot < n1)
+                    sum1 += (double)x[src];
+                else
+                    sum2 += (double)x[src];
+                slot++;
+            }
+        }
+        T[b] = sum1 / (double)n1 - sum2 / (double)(n - n1);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Kendall discordant-pair count for the Mallows kernel (Sec. 5)        */
+/* ------------------------------------------------------------------ */
+
+static uint64_t oracle_merge_count(uint32_t *a, uint32_t *tmp, uint32_t lo, uint32_t hi)
+{
+    uint32_t mid, i, j, t;
+    uint64_t inv;
+    if (hi - lo < 2)
+        return 0;
+    mid = lo + (hi - lo) / 2;
+    inv = oracle_merge_count(a, tmp, lo, mid) + oracle_merge_count(a, tmp, mid, hi);
+    i = lo;
+    j = mid;
+    t = lo;
+    while (i < mid && j < hi) {
+        if (a[i] <= a[j]) {
+            tmp[t++] = a[i++];
+        } else {
+            inv += mid - i;
+            tmp[t++] = a[j++];
+        }
+    }
+    while (i < mid)
+        tmp[t++] = a[i++];
+    while (j < hi)
+        tmp[t++] = a[j++];
+    memcpy(a + lo, tmp + lo, sizeof(uint32_t) * (hi - lo));
+    return inv;
+}
+
+/*
+ * n_dis(s, t) = #{i < j : (s(i) < s(j)) != (t(i) < t(j))} for permutations s,
+ * t of [0, n) in one-line notation: order the positions by s and count the
+ * inversions of t read in that order (merge sort, Knight 1966).
+ */
+uint64_t oracle_kendall_discordant(const uint32_t *s, const uint32_t *t, uint32_t n)
+{
+    uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *seq = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *tmp = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t i;
+    uint64_t inv;
+    for (i = 0; i < n; i++)
+        order[s[i]] = i;              /* order[r] = position holding rank r in s */
+    for (i = 0; i < n; i++)
+        seq[i] = t[order[i]];
+    inv = oracle_merge_count(seq, tmp, 0, n);
+    free(order);
+    free(seq);
+    free(tmp);
+    return inv;
+}
+
+/* Pairwise counts for consecutive pairs (perms[2p], perms[2p+1]), the pairing
+ * of the unbiased MMD estimate in Sec. 5. */
+void oracle_kendall_pairs(const uint32_t *perms, uint32_t n, uint64_t num_pairs, uint64_t *out)
+{
+    uint64_t p;
+    for (p = 0; p < num_pairs; p++)
+        out[p] = oracle_kendall_discordant(perms + (2 * p) * n, perms + (2 * p + 1) * n, n);
+}

@@ -1,0 +1,19 @@
+"""Shared pytest configuration.
+
+Tests marked ``gpu`` need a CUDA device and the compiled CUDA library; every
+other test runs on the CPU (the oracle, its pins, host-side logic, and the
+loading of the C-ABI library without compute calls).
+"""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled CUDA library")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
