@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 bijective shuffle.
+
+Workload (one "step"): one fused shuffle of n = 2^28 uniform random 64-bit
+keys (the paper's Sec. 6 payload) already resident in HBM: bijection, keep
+flags, in-tile scan, decoupled look-back, gather and compacted store, all in
+one launch of the library's kernel through the C ABI.  Inputs (2 GiB) are far
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Printed on one JSON line (rank 0):
+  value        shuffled elements per second, whole job (all ranks)
+  roofline     algorithmic bytes 2 * n * 8 per launch over the measured launch
+               time, against the measured HBM copy peak
+  e2e          the same metric through the C ABI from pinned host buffers,
+               host-to-device and device-to-host copies inside the timed region
+  cpu_baseline the CPU oracle, as it stands, on a bounded sample of the same
+               workload (the first slots of the same shuffle)
+  extra        worst-case padding (n = 2^28 + 12345) and the 4096-instance
+               uneven batch, batched launch vs one plain launch per instance
+
+`--impl reference` times the CPU oracle on this workload instead (bounded
+sample per step) and prints the same line with "impl": "reference".
+Multi-GPU (torchrun): every rank shuffles its own array (independent
+problems, weak scaling) with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+N_MAIN = 2**28
+N_WORST = 2**28 + 12345
+ELEM = 8
+SEED = 0
+ROUNDS = 24
+METRIC = "shuffled elements/s at n=2^28 uint64 (VariablePhilox bijective shuffle, fused single pass)"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_permute_u64_2p28.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
+    p.add_argument("--profile-n", type=int, default=0,
+                   help="only run warmup + steps launches of the uint64 shuffle at this n (for ncu)")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bshuffle_clocks_{os.getpid()}_{index}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, flag in zip(names, parts[3:7]):
+                    if flag.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed
+
+def dist_setup(gpus: int):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != gpus and world > 1:
+        raise SystemExit(f"--gpus {gpus} but WORLD_SIZE={world}")
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def cpu_oracle_sample(slots: int, trials: int):
+    """The oracle, as it stands, on the first `slots` outputs of the workload."""
+    import oracle
+    x = workloads.uniform_u64(N_MAIN, SEED)
+    oracle.permute_first(x, SEED, 1024)  # load + warm
+    times = []
+    for _ in range(trials):
+        t0 = time.perf_counter()
+        oracle.permute_first(x, SEED, slots)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args):
+    rank, world, _ = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
+    if rank != 0:
+        return
+    slots = 2**20
+    times = cpu_oracle_sample(slots, args.warmup + args.steps)[args.warmup:]
+    total = sum(times)
+    value = slots * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "elements/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "bijective shuffle of n=2^28 uniform uint64 keys, seed 0, 24 rounds",
+                   "n": N_MAIN, "elem_bytes": ELEM},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {slots} output slots of the n=2^28 uint64 shuffle per step"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU
+
+def timed_launches(fn, steps, stream, torch):
+    """Per-launch CUDA-event durations (ms) and the whole region (ms)."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    region0 = torch.cuda.Event(enable_timing=True)
+    region1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    region0.record(stream)
+    for k in range(steps):
+        starts[k].record(stream)
+        fn()
+        ends[k].record(stream)
+    region1.record(stream)
+    torch.cuda.synchronize()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return per, region0.elapsed_time(region1)
+
+
+def traffic_for(fingerprint: str):
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as fh:
+        d = json.load(fh)
+    if d.get("library_fingerprint") != fingerprint:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    from paper_2106_06161_gb300 import build as bsbuild
+    if rank == 0 or world == 1:
+        bsbuild.build()
+    barrier(world)
+    import paper_2106_06161_gb300 as bs
+    bs.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    seed = SEED + rank
+    host = workloads.uniform_u64(N_MAIN, seed)
+    x = torch.from_numpy(host.view(np.int64)).to(dev)
+    y = torch.empty_like(x)
+    xp, yp = x.data_ptr(), y.data_ptr()
+
+    def step():
+        bs.bshuffle_permute(xp, yp, N_MAIN, ELEM, seed, ROUNDS, sptr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if bs.get_error() != 0:
+        raise SystemExit("device error during warm-up")
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    clocks.start()
+    per, region_ms = timed_launches(step, args.steps, stream, torch)
+    clk = clocks.stop()
+    barrier(world)
+    if bs.get_error() != 0:
+        raise SystemExit("device error during the timed region")
+    region_ms = max_over_ranks(region_ms, world)
+    ms_per_step = region_ms / args.steps
+    value = N_MAIN * world * args.steps / (region_ms * 1e-3)
+    launch_ms = statistics.mean(per)
+
+    peak, peak_kind = measured_peaks()
+    algo_bytes = 2 * N_MAIN * ELEM
+    achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
+    fp = open(os.path.join(bsbuild.BUILD_DIR, "stamp.txt")).read().strip()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_for(fp), "peak_kind": peak_kind,
+                "kernel": "elem_tile_kernel<uint64, Gather, even k>",
+                "algorithmic_bytes_per_launch": algo_bytes}
+
+    # e2e: pinned host in -> device -> shuffle -> host out, every step
+    e2e_steps = max(3, min(20, args.steps // 10))
+    hin = torch.from_numpy(host.view(np.int64)).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(2):
+        x.copy_(hin, non_blocking=True)
+        step()
+        hout.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        x.copy_(hin, non_blocking=True)
+        step()
+        hout.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e = {"value": N_MAIN * world * e2e_steps / (e2e_ms * 1e-3), "unit": "elements/s",
+           "h2d_bytes_per_step": N_MAIN * ELEM, "d2h_bytes_per_step": N_MAIN * ELEM,
+           "ms_per_step": e2e_ms / e2e_steps, "steps": e2e_steps}
+    # the round trip is exact
+    if rank == 0:
+        idx = torch.randint(0, N_MAIN, (1 << 16,), device=dev)
+        src = bs.indices(N_MAIN, seed)[idx]
+        assert torch.equal(y[idx], x[src]), "shuffle output does not match its index sequence"
+    del hin, hout
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra = secondary(bs, torch, dev, stream)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        slots = 2**21
+        times = cpu_oracle_sample(slots, 8)
+        cores = 1
+        cpu = {"value": slots * len(times) / sum(times), "unit": "elements/s", "cores": cores,
+               "kind": "oracle",
+               "sample": f"first {slots} output slots of the same n=2^28 uint64 shuffle, 8 trials, "
+                         f"single-threaded C oracle"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "bijective shuffle of n=2^28 uniform uint64 keys per GPU, seed 0, 24 rounds",
+                       "n": N_MAIN, "elem_bytes": ELEM, "rounds": ROUNDS,
+                       "l2": "inputs (2 GiB) larger than L2, no flush",
+                       "parallelism": f"independent shuffles, {world} GPU(s)"},
+            "logical_gbps": achieved, "launch_ms": launch_ms,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
+            "cpu_baseline": cpu, "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def secondary(bs, torch, dev, stream):
+    """Worst-case padding and the uneven batch (one-off measurements)."""
+    out = {}
+    sptr = stream.cuda_stream
+    # n = 2^28 + 12345: domain 2^29, about half of the images dropped
+    host = workloads.uniform_u64(N_WORST, 1)
+    x = torch.from_numpy(host.view(np.int64)).to(dev)
+    y = torch.empty_like(x)
+    xp, yp = x.data_ptr(), y.data_ptr()
+    f = lambda: bs.bshuffle_permute(xp, yp, N_WORST, ELEM, 1, ROUNDS, sptr)  # noqa: E731
+    for _ in range(3):
+        f()
+    per, region = timed_launches(f, 20, stream, torch)
+    out["worst_case_2p28_plus_12345_u64"] = {
+        "elements_per_s": N_WORST * 20 / (region * 1e-3), "launch_ms": statistics.mean(per),
+        "logical_gbps": 2 * N_WORST * ELEM / (statistics.mean(per) * 1e-3) / 1e9}
+    del x, y
+
+    # 4096 uneven instances, int32: one batched launch vs one plain launch each
+    sizes = workloads.batched_sizes()
+    data = torch.from_numpy(workloads.batched_payloads(sizes)).to(dev)
+    res = torch.empty_like(data)
+    descs = bs.packed_descs(data, res, sizes, list(range(len(sizes))))
+    count = len(sizes)
+    dptr = descs.data_ptr()
+    fb = lambda: bs.bshuffle_batched(dptr, count, 4, ROUNDS, sptr)  # noqa: E731
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]) * 4
+    ins = [data.data_ptr() + int(o) for o in offs]
+    outs = [res.data_ptr() + int(o) for o in offs]
+    ns = [int(n) for n in sizes]
+
+    def plain_all():
+        for t in range(count):
+            bs.bshuffle_permute(ins[t], outs[t], ns[t], 4, t, ROUNDS, sptr)
+
+    for _ in range(3):
+        fb()
+    _, tb = timed_launches(fb, 10, stream, torch)
+    batched_ref = res.clone()
+    plain_all()
+    torch.cuda.synchronize()
+    _, tp = timed_launches(plain_all, 3, stream, torch)
+    same = bool(torch.equal(res, batched_ref))
+    out["batched_4096_uneven_int32"] = {
+        "batched_ms": tb / 10, "plain_ms": tp / 3, "speedup": (tp / 3) / (tb / 10),
+        "batched_shuffles_per_s": count / (tb / 10 * 1e-3), "plain_shuffles_per_s": count / (tp / 3 * 1e-3),
+        "total_elements": int(sizes.sum()), "batched_equals_plain": same}
+    return out
+
+
+def profile_case(args):
+    """warmup + steps plain launches of the uint64 shuffle at n = --profile-n."""
+    import torch
+    from paper_2106_06161_gb300 import build as bsbuild
+    bsbuild.build()
+    import paper_2106_06161_gb300 as bs
+    n = args.profile_n
+    x = torch.from_numpy(workloads.uniform_u64(n, SEED).view(np.int64)).cuda()
+    y = torch.empty_like(x)
+    sptr = torch.cuda.current_stream().cuda_stream
+    f = lambda: bs.bshuffle_permute(x.data_ptr(), y.data_ptr(), n, ELEM, SEED, ROUNDS, sptr)  # noqa: E731
+    for _ in range(args.warmup):
+        f()
+    per, region = timed_launches(f, args.steps, torch.cuda.current_stream(), torch)
+    if bs.get_error() != 0:
+        raise SystemExit("device error")
+    print(json.dumps({"profile_n": n, "launch_ms": per, "elements_per_s": n * args.steps / (region * 1e-3)}))
+
+
+def main():
+    args = parse()
+    if args.profile_n:
+        profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

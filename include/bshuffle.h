@@ -1,0 +1,189 @@
+/*
+ * bshuffle.h -- C ABI of the GB300 bijective-shuffle library (libbshuffle.so).
+ *
+ * The method is the "bijective shuffle" of Mitchell, Stokes, Frank and Holmes,
+ * "Bandwidth-Optimal Random Shuffling for GPUs" (arXiv 2106.06161):
+ *   - a keyed pseudo-random bijection f on the power-of-two domain [0, 2^k)
+ *     (VariablePhilox, Sec. 3.2, Listing 1), and
+ *   - Algorithm 1 (Sec. 4): evaluate b = f(i) for every i in [0, 2^k), keep the
+ *     images b < n, place the j-th kept image at output slot j (exclusive scan
+ *     of the keep flags) and gather Y[j] = X[b].
+ * Proposition 1 (Sec. 4) shows that deleting the images >= n from a uniform
+ * permutation of [0, 2^k) leaves a uniform permutation of [0, n).
+ *
+ * Every step runs on the GPU in one fused kernel per call: the bijection in
+ * registers, the compaction as an in-tile scan chained across tiles by
+ * decoupled look-back (single pass, Sec. 4 last paragraph and the
+ * "Bijective2" variant of Sec. 6), the gather of each kept element once, and a
+ * coalesced store into its compacted slot.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Domain.     k = max(ceil(log2 n), 4).  Sec. 4 pads to "the nearest power of
+ *             two"; the floor of 2^4 is a reading: with k <= 3 the left half
+ *             of the cipher has one bit, the cipher is affine over GF(2) and
+ *             reaches at most 2^k of the n! permutations.
+ * Rounds.     0 <= rounds <= BSHUFFLE_MAX_ROUNDS.  Sec. 5 recommends 24
+ *             (BSHUFFLE_DEFAULT_ROUNDS); 0 rounds is the identity bijection.
+ * Keys.       key[r] = low 32 bits of the r-th output of SplitMix64 seeded with
+ *             `seed` (Steele, Lea, Flood 2014).  The paper leaves the key
+ *             schedule open ("key[i]", Listing 1; Sec. 7).
+ * Sizes.      0 <= n <= BSHUFFLE_MAX_N.  n = 0 is a successful no-op.
+ * Elements.   elem_bytes is 1, 2, 4, 8, or a positive multiple of 16 (rows of
+ *             a matrix, moved whole).  Elements are raw bytes: the library
+ *             never looks at their values, so every dtype is bit-exact.
+ * Memory.     All data pointers are DEVICE pointers owned by the caller.  `in`
+ *             and `out` must not overlap (the shuffle is not in place, Sec. 7)
+ *             and must be aligned to min(elem_bytes, 16) bytes.
+ * Streams.    `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *             default stream).  Calls are asynchronous with respect to the
+ *             host and ordered on `stream`.
+ * Workspace.  The library owns a small per-(device, stream) workspace: a
+ *             tile-status word per tile (8 bytes per 2^11 domain indices), a
+ *             tile ticket, a completion counter and an error word.  It is
+ *             allocated with cudaMalloc on the first call that needs it (make
+ *             that first call before capturing the stream into a CUDA graph)
+ *             and reused; bshuffle_release_workspaces() frees it.  Calls
+ *             that share a stream share its workspace and must not run
+ *             concurrently with each other, which stream order guarantees.
+ * Errors.     Every function returns BSHUFFLE_OK (0) or a negative code.
+ *             Argument errors are detected on the host before any launch and
+ *             leave the output untouched.  Device-side errors (a look-back
+ *             wait that ran past its time limit, an out-of-range slot) are
+ *             recorded in the workspace's error word and returned by
+ *             bshuffle_get_error(); the kernels never trap.
+ * No fallback. There is no CPU path.  Without a CUDA device every compute
+ *             call returns BSHUFFLE_ERR_CUDA.
+ */
+#ifndef BSHUFFLE_H
+#define BSHUFFLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSHUFFLE_OK 0
+#define BSHUFFLE_ERR_NULL (-1)              /* a required pointer is NULL */
+#define BSHUFFLE_ERR_ELEM (-2)              /* unsupported elem_bytes / idx_bytes */
+#define BSHUFFLE_ERR_ROUNDS (-3)            /* rounds > BSHUFFLE_MAX_ROUNDS */
+#define BSHUFFLE_ERR_TOO_LARGE (-4)         /* n > BSHUFFLE_MAX_N */
+#define BSHUFFLE_ERR_ALIAS (-5)             /* in and out overlap */
+#define BSHUFFLE_ERR_ALIGN (-6)             /* pointer not aligned to min(elem_bytes, 16) */
+#define BSHUFFLE_ERR_CUDA (-7)              /* a CUDA runtime call failed */
+#define BSHUFFLE_ERR_LOOKBACK_TIMEOUT (-8)  /* device: a look-back wait ran out of time */
+#define BSHUFFLE_ERR_DEVICE_BOUNDS (-9)     /* device: an output slot fell outside [0, n) */
+#define BSHUFFLE_ERR_INVALID (-10)          /* other invalid argument (e.g. batch count) */
+
+#define BSHUFFLE_DEFAULT_ROUNDS 24u
+#define BSHUFFLE_MAX_ROUNDS 64u
+/* Largest supported length: slots and domain indices are 32-bit (k <= 32). */
+#define BSHUFFLE_MAX_N 4294967295ull
+
+/* One instance of a batched shuffle (device memory, see bshuffle_batched). */
+typedef struct bshuffle_desc {
+    const void *in;   /* device pointer to n elements */
+    void *out;        /* device pointer to n elements, disjoint from every in/out */
+    uint64_t n;       /* instance length, 0 <= n <= BSHUFFLE_MAX_N */
+    uint64_t seed;    /* key seed of this instance */
+} bshuffle_desc;
+
+/*
+ * Y[j] = X[f(i_j)] for j in [0, n), where i_j is the j-th domain index, in
+ * increasing order, whose image f(i_j) is below n (Algorithm 1, Sec. 4; f is
+ * VariablePhilox of Sec. 3.2 with the keys of `seed`).
+ *   in, out     device buffers of n * elem_bytes bytes each (caller-owned)
+ *   n           number of elements
+ *   elem_bytes  1, 2, 4, 8 or a multiple of 16
+ *   seed        key seed; rounds: cipher rounds (24 recommended)
+ *   stream      cudaStream_t as void*
+ * Returns BSHUFFLE_OK once the kernel is enqueued.
+ */
+int bshuffle_permute(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                     uint32_t rounds, void *stream);
+
+/*
+ * out_idx[j] = f(i_j): the source index of each output slot of
+ * bshuffle_permute with the same (n, seed, rounds), i.e. bshuffle_permute of
+ * the iota input 0, 1, ..., n-1 (Algorithm 1, Sec. 4).
+ *   out_idx     device buffer of n * idx_bytes bytes
+ *   idx_bytes   4 (uint32 indices) or 8 (uint64 indices)
+ */
+int bshuffle_indices(void *out_idx, uint32_t idx_bytes, uint64_t n, uint64_t seed, uint32_t rounds,
+                     void *stream);
+
+/*
+ * The inverse shuffle, a scatter through the same bijection:
+ * out[f(i_j)] = in[j], so bshuffle_inverse(bshuffle_permute(x)) == x for equal
+ * (n, seed, rounds).  Arguments as for bshuffle_permute.  (The paper notes
+ * that a scatter is the inverse of a gather, Sec. 2.2.)
+ */
+int bshuffle_inverse(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                     uint32_t rounds, void *stream);
+
+/*
+ * `count` independent shuffles in one launch.  Instance t reads d_descs[t]
+ * (DEVICE memory) and produces exactly bshuffle_permute(in, out, n,
+ * elem_bytes, seed, rounds) for its own (in, out, n, seed).  All instances
+ * share elem_bytes and rounds; no two instances' buffers may overlap.
+ *   d_descs     device array of `count` bshuffle_desc (caller-owned; read by
+ *               the kernels, so it must stay valid until the stream reaches
+ *               the end of this call)
+ *   count       1 <= count <= 2^24 (0 is a no-op)
+ * The library keeps per-instance tile tables in the stream's workspace.  The
+ * call enqueues a small planning kernel and one persistent shuffle kernel.
+ */
+int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem_bytes, uint32_t rounds,
+                     void *stream);
+
+/*
+ * Synchronises `stream`, then returns and clears the first device-side error
+ * recorded by calls on that stream since the last bshuffle_get_error:
+ * BSHUFFLE_OK, BSHUFFLE_ERR_LOOKBACK_TIMEOUT or BSHUFFLE_ERR_DEVICE_BOUNDS (or
+ * BSHUFFLE_ERR_CUDA if synchronising failed).  A stream without a workspace
+ * has no recorded errors.
+ */
+int bshuffle_get_error(void *stream);
+
+/* Static English text for a return code; never NULL. */
+const char *bshuffle_error_string(int code);
+
+/*
+ * Host-side helpers (no GPU needed).  The domain exponent k of length n
+ * (0 for n = 0) and the round keys of a seed, exactly as the kernels use
+ * them.  keys must hold `rounds` entries.  Return BSHUFFLE_OK or an error.
+ */
+int bshuffle_domain_bits(uint64_t n, uint32_t *k);
+int bshuffle_round_keys(uint64_t seed, uint32_t rounds, uint32_t *keys);
+
+/*
+ * Frees every workspace the library allocated (all devices and streams).
+ * The caller must ensure no call of this library is still running.
+ */
+int bshuffle_release_workspaces(void);
+
+/*
+ * Time limit of one look-back wait in nanoseconds (default 2e9).  When a
+ * wait runs out the kernel records BSHUFFLE_ERR_LOOKBACK_TIMEOUT, skips its
+ * stores and lets later tiles finish.  Values below 1e6 are raised to 1e6.
+ */
+int bshuffle_set_lookback_timeout_ns(uint64_t ns);
+
+/*
+ * Test hook: the tile with this index, in every following call, does not
+ * publish its tile status, so that its successors' look-back waits run out
+ * and report BSHUFFLE_ERR_LOOKBACK_TIMEOUT.  Pass -1 to switch it off
+ * (the default).
+ */
+int bshuffle_debug_skip_publish(int64_t tile);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int bshuffle_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSHUFFLE_H */

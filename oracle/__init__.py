@@ -62,6 +62,7 @@ def _load():
             "oracle_indices": (u64, [p, u64, u64, u32]),
             "oracle_permute_k": (u64, [p, p, u64, u32, u32, u64, u32]),
             "oracle_permute": (u64, [p, p, u64, u32, u64, u32]),
+            "oracle_permute_first": (u64, [p, p, u64, u32, u64, u32, u64]),
             "oracle_inverse": (u64, [p, p, u64, u32, u64, u32]),
             "oracle_sample_permutations": (None, [p, u32, u64, u64, u32]),
             "oracle_fisher_yates": (None, [p, u64, u32, u64]),
@@ -148,6 +149,20 @@ def permute(x: np.ndarray, seed: int, rounds: int = DEFAULT_ROUNDS, k: int | Non
     got = _load().oracle_permute_k(_ptr(x), _ptr(out), n, elem_bytes, kk, seed & (2**64 - 1), rounds)
     if got != n:
         raise ValueError(f"domain 2^{kk} kept {got} of {n} elements")
+    return out
+
+
+def permute_first(x: np.ndarray, seed: int, slots: int, rounds: int = DEFAULT_ROUNDS) -> np.ndarray:
+    """The first `slots` rows of permute(x, seed, rounds), computed alone."""
+    x = np.ascontiguousarray(x)
+    n = x.shape[0]
+    slots = min(slots, n)
+    out = np.empty((max(slots, 1),) + x.shape[1:], dtype=x.dtype)
+    if n == 0 or slots == 0:
+        return out[:0]
+    got = _load().oracle_permute_first(_ptr(x), _ptr(out), n, x.nbytes // n, seed & (2**64 - 1), rounds, slots)
+    if got != slots:
+        raise ValueError("permute_first wrote a wrong count")
     return out
 
 

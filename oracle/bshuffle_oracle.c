@@ -254,6 +254,31 @@ uint64_t oracle_permute(const void *in, void *out, uint64_t n, uint32_t elem_byt
     return oracle_permute_k(in, out, n, elem_bytes, oracle_domain_bits(n), seed, rounds);
 }
 
+/* The first `slots` output elements of oracle_permute (the same loop, stopped
+ * once `slots` elements have been written): a bounded sample of a large
+ * shuffle for CPU timing. */
+uint64_t oracle_permute_first(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                              uint32_t rounds, uint64_t slots)
+{
+    const unsigned char *x = (const unsigned char *)in;
+    unsigned char *y = (unsigned char *)out;
+    uint32_t keys[256];
+    uint32_t k = oracle_domain_bits(n);
+    uint64_t domain, i, out_idx = 0;
+    if (n == 0 || rounds > 256 || k > 40)
+        return 0;
+    oracle_round_keys(seed, rounds, keys);
+    domain = (uint64_t)1 << k;
+    for (i = 0; i < domain && out_idx < slots; i++) {
+        uint64_t b = oracle_varphilox(i, k, keys, rounds);
+        if (b < n) {
+            memcpy(y + out_idx * elem_bytes, x + b * elem_bytes, elem_bytes);
+            out_idx++;
+        }
+    }
+    return out_idx;
+}
+
 /* The inverse shuffle: out[f(i_j)] = in[j], so that inverse(permute(x)) = x. */
 uint64_t oracle_inverse(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                         uint32_t rounds)

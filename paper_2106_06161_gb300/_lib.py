@@ -1,0 +1,145 @@
+"""ctypes binding of libbshuffle.so with the C names of include/bshuffle.h.
+
+Argument marshalling only: every function forwards to the C ABI of the
+in-tree library and raises :class:`BShuffleError` on a negative return code.
+There is no fallback: if the library has not been built, loading fails with
+an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbshuffle.so")
+
+BSHUFFLE_OK = 0
+BSHUFFLE_ERR_NULL = -1
+BSHUFFLE_ERR_ELEM = -2
+BSHUFFLE_ERR_ROUNDS = -3
+BSHUFFLE_ERR_TOO_LARGE = -4
+BSHUFFLE_ERR_ALIAS = -5
+BSHUFFLE_ERR_ALIGN = -6
+BSHUFFLE_ERR_CUDA = -7
+BSHUFFLE_ERR_LOOKBACK_TIMEOUT = -8
+BSHUFFLE_ERR_DEVICE_BOUNDS = -9
+BSHUFFLE_ERR_INVALID = -10
+DEFAULT_ROUNDS = 24
+MAX_ROUNDS = 64
+MAX_N = 2**32 - 1
+
+# Every function the header declares, with (restype, argtypes).
+_u32, _u64, _i64, _p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p
+_int, _str = ctypes.c_int, ctypes.c_char_p
+SIGNATURES = {
+    "bshuffle_permute": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
+    "bshuffle_indices": (_int, [_p, _u32, _u64, _u64, _u32, _p]),
+    "bshuffle_inverse": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
+    "bshuffle_batched": (_int, [_p, _u32, _u32, _u32, _p]),
+    "bshuffle_get_error": (_int, [_p]),
+    "bshuffle_error_string": (_str, [_int]),
+    "bshuffle_domain_bits": (_int, [_u64, ctypes.POINTER(_u32)]),
+    "bshuffle_round_keys": (_int, [_u64, _u32, _p]),
+    "bshuffle_release_workspaces": (_int, []),
+    "bshuffle_set_lookback_timeout_ns": (_int, [_u64]),
+    "bshuffle_debug_skip_publish": (_int, [_i64]),
+    "bshuffle_version": (_int, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BShuffleError(RuntimeError):
+    """A negative return code of libbshuffle."""
+
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        msg = error_string(code) if _lib is not None else f"error {code}"
+        super().__init__(f"{where}: {msg} (code {code})" if where else f"{msg} (code {code})")
+
+
+def load() -> ctypes.CDLL:
+    """Load the in-tree libbshuffle.so (built by paper_2106_06161_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with `python -m paper_2106_06161_gb300.build` "
+                    "(or __graft_entry__.build()); there is no CPU fallback")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+        return _lib
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise BShuffleError(rc, where)
+    return rc
+
+
+def error_string(code: int) -> str:
+    return load().bshuffle_error_string(code).decode()
+
+
+def bshuffle_permute(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, seed: int,
+                     rounds: int = DEFAULT_ROUNDS, stream: int = 0) -> None:
+    _check(load().bshuffle_permute(in_ptr, out_ptr, n, elem_bytes, seed & (2**64 - 1), rounds, stream),
+           "bshuffle_permute")
+
+
+def bshuffle_indices(out_ptr: int, idx_bytes: int, n: int, seed: int, rounds: int = DEFAULT_ROUNDS,
+                     stream: int = 0) -> None:
+    _check(load().bshuffle_indices(out_ptr, idx_bytes, n, seed & (2**64 - 1), rounds, stream),
+           "bshuffle_indices")
+
+
+def bshuffle_inverse(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, seed: int,
+                     rounds: int = DEFAULT_ROUNDS, stream: int = 0) -> None:
+    _check(load().bshuffle_inverse(in_ptr, out_ptr, n, elem_bytes, seed & (2**64 - 1), rounds, stream),
+           "bshuffle_inverse")
+
+
+def bshuffle_batched(descs_ptr: int, count: int, elem_bytes: int, rounds: int = DEFAULT_ROUNDS,
+                     stream: int = 0) -> None:
+    _check(load().bshuffle_batched(descs_ptr, count, elem_bytes, rounds, stream), "bshuffle_batched")
+
+
+def bshuffle_get_error(stream: int = 0) -> int:
+    """Device-side error recorded on the stream since the last call (0 = none)."""
+    return load().bshuffle_get_error(stream)
+
+
+def bshuffle_domain_bits(n: int) -> int:
+    k = _u32(0)
+    _check(load().bshuffle_domain_bits(n, ctypes.byref(k)), "bshuffle_domain_bits")
+    return k.value
+
+
+def bshuffle_round_keys(seed: int, rounds: int = DEFAULT_ROUNDS) -> list[int]:
+    buf = (_u32 * max(rounds, 1))()
+    _check(load().bshuffle_round_keys(seed & (2**64 - 1), rounds, ctypes.addressof(buf)),
+           "bshuffle_round_keys")
+    return [int(buf[i]) for i in range(rounds)]
+
+
+def bshuffle_release_workspaces() -> None:
+    _check(load().bshuffle_release_workspaces(), "bshuffle_release_workspaces")
+
+
+def bshuffle_set_lookback_timeout_ns(ns: int) -> None:
+    _check(load().bshuffle_set_lookback_timeout_ns(ns), "bshuffle_set_lookback_timeout_ns")
+
+
+def bshuffle_debug_skip_publish(tile: int) -> None:
+    _check(load().bshuffle_debug_skip_publish(tile), "bshuffle_debug_skip_publish")
+
+
+def bshuffle_version() -> int:
+    return load().bshuffle_version()

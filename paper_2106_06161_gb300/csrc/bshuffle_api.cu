@@ -1,0 +1,400 @@
+// C ABI of libbshuffle: argument checking, the key schedule, the per-stream
+// workspace and the launches.  The data path is entirely on the GPU; this
+// file never touches element data.
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bshuffle.h"
+#include "bshuffle_internal.h"
+
+namespace {
+
+using bsh::Geometry;
+using bsh::Mode;
+using bsh::TileArgs;
+using bsh::WsHeader;
+
+constexpr uint32_t kKMin = 4;                 // domain floor 2^4 (see bshuffle.h)
+constexpr size_t kHeaderBytes = 256;          // header slot, keeps the status array aligned
+constexpr uint64_t kMinStatusWords = 4096;
+
+std::atomic<uint64_t> g_timeout_ns{2000000000ull};
+std::atomic<int64_t> g_skip_publish{-1};
+
+// ------------------------------------------------------------------ host math
+
+uint32_t domain_bits_of(uint64_t n)
+{
+    if (n == 0) return 0;
+    uint32_t k = 0;
+    while (k < 64 && (uint64_t{1} << k) < n) ++k;
+    return k < kKMin ? kKMin : k;
+}
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the round-key schedule.
+uint64_t splitmix64(uint64_t &state)
+{
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void fill_keys(uint64_t seed, uint32_t rounds, uint32_t *keys)
+{
+    uint64_t state = seed;
+    for (uint32_t r = 0; r < rounds; ++r) keys[r] = static_cast<uint32_t>(splitmix64(state));
+}
+
+Geometry geometry_of(uint64_t n)
+{
+    Geometry g{};
+    g.n = static_cast<uint32_t>(n);
+    g.k = domain_bits_of(n);
+    g.L = g.k / 2;
+    g.R = g.k - g.L;
+    g.lmask = (1u << g.L) - 1u;
+    g.rmask = g.R >= 32 ? 0xffffffffu : ((1u << g.R) - 1u);
+    g.domain = uint64_t{1} << g.k;
+    return g;
+}
+
+// ------------------------------------------------------------------ workspace
+
+struct Workspace {
+    void *base = nullptr;
+    uint64_t status_words = 0;
+    void *aux = nullptr;       // batched plan tables
+    size_t aux_bytes = 0;
+    WsHeader *header() const { return static_cast<WsHeader *>(base); }
+    uint64_t *status() const
+    {
+        return reinterpret_cast<uint64_t *>(static_cast<char *>(base) + kHeaderBytes);
+    }
+};
+
+std::mutex g_mutex;
+std::map<std::pair<int, uintptr_t>, Workspace> g_workspaces;
+
+int cuda_fail(cudaError_t e)
+{
+    (void)e;
+    cudaGetLastError();  // clear the sticky launch error of this thread
+    return BSHUFFLE_ERR_CUDA;
+}
+
+uint64_t round_up_pow2(uint64_t v)
+{
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Returns the stream's workspace with room for `words` tile-status words,
+// allocating or growing it (growing synchronises the stream first).
+int acquire_workspace(cudaStream_t stream, uint64_t words, Workspace **out)
+{
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lock(g_mutex);
+    Workspace &ws = g_workspaces[{device, reinterpret_cast<uintptr_t>(stream)}];
+    if (ws.base != nullptr && ws.status_words >= words) {
+        *out = &ws;
+        return BSHUFFLE_OK;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cap != cudaStreamCaptureStatusNone) return BSHUFFLE_ERR_INVALID;  // allocate before capture
+
+    const uint64_t cap_words = round_up_pow2(words < kMinStatusWords ? kMinStatusWords : words);
+    WsHeader keep{};
+    keep.tag = 1;
+    if (ws.base != nullptr) {
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaMemcpy(&keep, ws.base, sizeof(keep), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e);
+        cudaFree(ws.base);
+        ws.base = nullptr;
+        ws.status_words = 0;
+        keep.ticket = 0;
+        keep.done = 0;
+        keep.batch_ticket = 0;
+        keep.batch_done = 0;
+        keep.tag = 1;  // the new status array is zeroed: tag 0 never matches
+    }
+    void *base = nullptr;
+    const size_t bytes = kHeaderBytes + cap_words * sizeof(uint64_t);
+    e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaMemsetAsync(base, 0, bytes, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base, &keep, sizeof(keep), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        return cuda_fail(e);
+    }
+    ws.base = base;
+    ws.status_words = cap_words;
+    *out = &ws;
+    return BSHUFFLE_OK;
+}
+
+// ------------------------------------------------------------------ checks
+
+bool valid_elem(uint32_t elem_bytes)
+{
+    return elem_bytes == 1 || elem_bytes == 2 || elem_bytes == 4 || elem_bytes == 8 ||
+           (elem_bytes != 0 && elem_bytes % 16 == 0);
+}
+
+uint32_t align_of(uint32_t elem_bytes) { return elem_bytes < 16 ? elem_bytes : 16; }
+
+int check_buffers(const void *in, const void *out, uint64_t n, uint32_t elem_bytes)
+{
+    if (in == nullptr || out == nullptr) return BSHUFFLE_ERR_NULL;
+    if (elem_bytes != 0 && n > UINT64_MAX / elem_bytes) return BSHUFFLE_ERR_TOO_LARGE;
+    const uint64_t bytes = n * elem_bytes;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
+    const uint32_t al = align_of(elem_bytes);
+    if (a % al != 0 || b % al != 0) return BSHUFFLE_ERR_ALIGN;
+    if (a < b + bytes && b < a + bytes) return BSHUFFLE_ERR_ALIAS;
+    return BSHUFFLE_OK;
+}
+
+int check_common(uint64_t n, uint32_t rounds)
+{
+    if (rounds > BSHUFFLE_MAX_ROUNDS) return BSHUFFLE_ERR_ROUNDS;
+    if (n > BSHUFFLE_MAX_N) return BSHUFFLE_ERR_TOO_LARGE;
+    return BSHUFFLE_OK;
+}
+
+// One fused launch over the whole domain of n.
+int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed, uint32_t rounds,
+              Mode mode, void *stream_ptr)
+{
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    TileArgs a{};
+    a.in = in;
+    a.out = out;
+    a.g = geometry_of(n);
+    a.rounds = rounds;
+    a.elem_bytes = elem_bytes;
+    a.skip_publish_tile = g_skip_publish.load();
+    a.timeout_ns = g_timeout_ns.load();
+    fill_keys(seed, rounds, a.keys);
+    const bool rows = (mode == Mode::Gather || mode == Mode::Scatter) && elem_bytes > 16;
+    const uint64_t tile = rows ? bsh::rows_tile_size() : bsh::elem_tile_size(elem_bytes, mode);
+    const uint64_t tiles = (a.g.domain + tile - 1) / tile;
+    a.num_tiles = static_cast<uint32_t>(tiles);
+    Workspace *ws = nullptr;
+    const int rc = acquire_workspace(stream, tiles, &ws);
+    if (rc != BSHUFFLE_OK) return rc;
+    a.ws = ws->header();
+    a.status = ws->status();
+    const cudaError_t e = rows ? bsh::launch_rows(a, mode, stream) : bsh::launch_elem(a, mode, elem_bytes, stream);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int bshuffle_version(void) { return 100; }
+
+int bshuffle_domain_bits(uint64_t n, uint32_t *k)
+{
+    if (k == nullptr) return BSHUFFLE_ERR_NULL;
+    if (n > BSHUFFLE_MAX_N) return BSHUFFLE_ERR_TOO_LARGE;
+    *k = domain_bits_of(n);
+    return BSHUFFLE_OK;
+}
+
+int bshuffle_round_keys(uint64_t seed, uint32_t rounds, uint32_t *keys)
+{
+    if (rounds > BSHUFFLE_MAX_ROUNDS) return BSHUFFLE_ERR_ROUNDS;
+    if (keys == nullptr && rounds > 0) return BSHUFFLE_ERR_NULL;
+    fill_keys(seed, rounds, keys);
+    return BSHUFFLE_OK;
+}
+
+int bshuffle_permute(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed, uint32_t rounds,
+                     void *stream)
+{
+    int rc = check_common(n, rounds);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (!valid_elem(elem_bytes)) return BSHUFFLE_ERR_ELEM;
+    if (n == 0) return BSHUFFLE_OK;
+    rc = check_buffers(in, out, n, elem_bytes);
+    if (rc != BSHUFFLE_OK) return rc;
+    return run_fused(in, out, n, elem_bytes, seed, rounds, Mode::Gather, stream);
+}
+
+int bshuffle_inverse(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed, uint32_t rounds,
+                     void *stream)
+{
+    int rc = check_common(n, rounds);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (!valid_elem(elem_bytes)) return BSHUFFLE_ERR_ELEM;
+    if (n == 0) return BSHUFFLE_OK;
+    rc = check_buffers(in, out, n, elem_bytes);
+    if (rc != BSHUFFLE_OK) return rc;
+    return run_fused(in, out, n, elem_bytes, seed, rounds, Mode::Scatter, stream);
+}
+
+int bshuffle_indices(void *out_idx, uint32_t idx_bytes, uint64_t n, uint64_t seed, uint32_t rounds, void *stream)
+{
+    int rc = check_common(n, rounds);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (idx_bytes != 4 && idx_bytes != 8) return BSHUFFLE_ERR_ELEM;
+    if (n == 0) return BSHUFFLE_OK;
+    if (out_idx == nullptr) return BSHUFFLE_ERR_NULL;
+    if (reinterpret_cast<uintptr_t>(out_idx) % idx_bytes != 0) return BSHUFFLE_ERR_ALIGN;
+    return run_fused(nullptr, out_idx, n, idx_bytes, seed, rounds, idx_bytes == 4 ? Mode::Index32 : Mode::Index64,
+                     stream);
+}
+
+int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem_bytes, uint32_t rounds, void *stream)
+{
+    if (rounds > BSHUFFLE_MAX_ROUNDS) return BSHUFFLE_ERR_ROUNDS;
+    if (count == 0) return BSHUFFLE_OK;
+    if (d_descs == nullptr) return BSHUFFLE_ERR_NULL;
+    if (elem_bytes != 1 && elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16)
+        return BSHUFFLE_ERR_ELEM;
+    if (count > (1u << 24)) return BSHUFFLE_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_descs) % alignof(bshuffle_desc) != 0) return BSHUFFLE_ERR_ALIGN;
+    static_assert(sizeof(bshuffle_desc) == sizeof(bsh::BatchDesc), "descriptor layouts differ");
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *ws = nullptr;
+    int rc = acquire_workspace(s, kMinStatusWords, &ws);
+    if (rc != BSHUFFLE_OK) return rc;
+    auto up = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+    const size_t plan_off = 0;
+    const size_t prefix_off = up(plan_off + sizeof(bsh::BatchPlan) * count);
+    const size_t total_off = up(prefix_off + sizeof(uint64_t) * (static_cast<size_t>(count) + 1));
+    const size_t ring_off = up(total_off + sizeof(uint64_t));
+    const size_t need = ring_off + sizeof(uint64_t) * bsh::batch_ring_words();
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (ws->aux_bytes < need) {
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            cudaError_t e = cudaStreamIsCapturing(s, &cap);
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (cap != cudaStreamCaptureStatusNone) return BSHUFFLE_ERR_INVALID;
+            if (ws->aux != nullptr) {
+                e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) return cuda_fail(e);
+                cudaFree(ws->aux);
+                ws->aux = nullptr;
+                ws->aux_bytes = 0;
+            }
+            const size_t bytes = round_up_pow2(need);
+            e = cudaMalloc(&ws->aux, bytes);
+            if (e != cudaSuccess) {
+                ws->aux = nullptr;
+                return cuda_fail(e);
+            }
+            ws->aux_bytes = bytes;
+        }
+    }
+    char *aux = static_cast<char *>(ws->aux);
+    bsh::BatchArgs a{};
+    a.descs = reinterpret_cast<const bsh::BatchDesc *>(d_descs);
+    a.plan = reinterpret_cast<bsh::BatchPlan *>(aux + plan_off);
+    a.tile_prefix = reinterpret_cast<uint64_t *>(aux + prefix_off);
+    a.total_tiles = reinterpret_cast<uint64_t *>(aux + total_off);
+    a.status = reinterpret_cast<uint64_t *>(aux + ring_off);
+    a.count = count;
+    a.rounds = rounds;
+    a.elem_bytes = elem_bytes;
+    a.timeout_ns = g_timeout_ns.load();
+    a.skip_publish_tile = g_skip_publish.load();
+    a.ws = ws->header();
+    const cudaError_t e = bsh::launch_batched(a, s);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
+int bshuffle_get_error(void *stream_ptr)
+{
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lock(g_mutex);
+    auto it = g_workspaces.find({device, reinterpret_cast<uintptr_t>(stream)});
+    if (it == g_workspaces.end() || it->second.base == nullptr) return BSHUFFLE_OK;
+    WsHeader h{};
+    e = cudaMemcpy(&h, it->second.base, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (h.error != 0) {
+        const size_t off = offsetof(WsHeader, error);
+        const size_t len = offsetof(WsHeader, error_info) + sizeof(h.error_info) - off;
+        e = cudaMemsetAsync(static_cast<char *>(it->second.base) + off, 0, len, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return h.error;
+}
+
+const char *bshuffle_error_string(int code)
+{
+    switch (code) {
+    case BSHUFFLE_OK: return "success";
+    case BSHUFFLE_ERR_NULL: return "a required pointer is NULL";
+    case BSHUFFLE_ERR_ELEM: return "unsupported element width (use 1, 2, 4, 8 or a multiple of 16 bytes; indices 4 or 8)";
+    case BSHUFFLE_ERR_ROUNDS: return "too many cipher rounds (at most 64)";
+    case BSHUFFLE_ERR_TOO_LARGE: return "length above the supported maximum (2^32 - 1 elements)";
+    case BSHUFFLE_ERR_ALIAS: return "input and output buffers overlap (the shuffle is not in place)";
+    case BSHUFFLE_ERR_ALIGN: return "buffer not aligned to min(element width, 16) bytes";
+    case BSHUFFLE_ERR_CUDA: return "a CUDA runtime call failed (no device, launch failure or stream error)";
+    case BSHUFFLE_ERR_LOOKBACK_TIMEOUT: return "device: a look-back wait ran past its time limit; output is invalid";
+    case BSHUFFLE_ERR_DEVICE_BOUNDS: return "device: an output slot fell outside [0, n); output is invalid";
+    case BSHUFFLE_ERR_INVALID: return "invalid argument or state (batch count, or workspace growth during graph capture)";
+    default: return "unknown bshuffle error code";
+    }
+}
+
+int bshuffle_release_workspaces(void)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    int rc = BSHUFFLE_OK;
+    for (auto &kv : g_workspaces) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cudaSetDevice(kv.first.first) != cudaSuccess) rc = BSHUFFLE_ERR_CUDA;
+        if (kv.second.base != nullptr && cudaFree(kv.second.base) != cudaSuccess) rc = BSHUFFLE_ERR_CUDA;
+        if (kv.second.aux != nullptr && cudaFree(kv.second.aux) != cudaSuccess) rc = BSHUFFLE_ERR_CUDA;
+        cudaSetDevice(cur);
+    }
+    g_workspaces.clear();
+    return rc;
+}
+
+int bshuffle_set_lookback_timeout_ns(uint64_t ns)
+{
+    g_timeout_ns.store(ns < 1000000ull ? 1000000ull : ns);
+    return BSHUFFLE_OK;
+}
+
+int bshuffle_debug_skip_publish(int64_t tile)
+{
+    g_skip_publish.store(tile < 0 ? -1 : tile);
+    return BSHUFFLE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,275 @@
+// Device building blocks of the fused bijective shuffle (sm_103a):
+//   * the VariablePhilox round (Sec. 3.2) on 32-bit registers,
+//   * the tile-status protocol of single-pass decoupled look-back
+//     (Merrill and Garland 2016, the scan the paper fuses in Sec. 4 / Sec. 6),
+//   * the in-tile scan of keep flags (Algorithm 1's exclusive scan).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bshuffle_internal.h"
+
+namespace bsh {
+namespace dev {
+
+// Philox multiplier M0 of Listing 1 (chosen by Salmon et al.).
+constexpr uint64_t kM0 = 0xD2B74407B1CE6E93ull;
+constexpr uint32_t kFull = 0xffffffffu;
+
+// Error codes written into WsHeader::error (same values as bshuffle.h).
+constexpr int kErrLookbackTimeout = -8;
+constexpr int kErrDeviceBounds = -9;
+
+// ------------------------------------------------------------------ cipher
+
+// One VariablePhilox round on the split state (left: L bits, right: R bits).
+// The 64-bit product M0 * left supplies F (its high word, XORed with the
+// round key and the right half into the new left half, L' = F_k(L) xor R)
+// and the bijection B (its low word).  For odd k, G shifts B up one bit and
+// moves the top bit b of the old right half in underneath, so the new right
+// half carries L + 1 bits.  For even k the right half is left unmasked
+// between rounds: only its low L bits are read by the next round, and the
+// caller masks it once at the end.
+template <bool ODD>
+__device__ __forceinline__ void cipher_round(uint32_t &left, uint32_t &right, uint32_t key,
+                                             uint32_t L, uint32_t lmask, uint32_t rmask)
+{
+    const uint64_t prod = kM0 * static_cast<uint64_t>(left);
+    const uint32_t hi = static_cast<uint32_t>(prod >> 32);
+    uint32_t lo = static_cast<uint32_t>(prod);
+    if (ODD) lo = (lo << 1) | (right >> L);
+    left = (hi ^ key ^ right) & lmask;
+    right = ODD ? (lo & rmask) : lo;
+}
+
+// ITEMS independent evaluations, rounds outer so that the ITEMS dependency
+// chains interleave and each round key is loaded once per thread.
+template <bool ODD, int ITEMS>
+__device__ __forceinline__ void cipher_items(uint32_t (&left)[ITEMS], uint32_t (&right)[ITEMS],
+                                             const uint32_t *keys, uint32_t rounds, const Geometry &g)
+{
+    const uint32_t L = g.L, lmask = g.lmask, rmask = g.rmask;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t key = keys[r];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) cipher_round<ODD>(left[j], right[j], key, L, lmask, rmask);
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) right[j] &= rmask;
+}
+
+// ------------------------------------------------------------------ memory helpers
+
+__device__ __forceinline__ uint64_t ld_relaxed_gpu(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void record_error(WsHeader *ws, int code, uint64_t info)
+{
+    if (atomicCAS(&ws->error, 0, code) == 0)
+        atomicExch(reinterpret_cast<unsigned long long *>(&ws->error_info),
+                   static_cast<unsigned long long>(info));
+}
+
+// ------------------------------------------------------------------ tile status
+
+// A tile-status word: tag (31 bits) | inclusive flag (1 bit) | value (32 bits).
+// The tag identifies the launch; a word with another tag reads as "not yet
+// published".  value is the tile's aggregate (flag 0) or its inclusive
+// prefix (flag 1).
+__device__ __forceinline__ uint64_t status_word(uint32_t tag, bool inclusive, uint32_t value)
+{
+    return (static_cast<uint64_t>(tag) << 33) | (static_cast<uint64_t>(inclusive) << 32) | value;
+}
+
+__device__ __forceinline__ uint32_t next_tag(uint32_t tag)
+{
+    return tag >= 0x7fffffffu ? 1u : tag + 1u;
+}
+
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(kFull, v, d);
+        if (lane >= static_cast<uint32_t>(d)) v += u;
+    }
+    return v;
+}
+
+// Where the tile-status words of a launch live and how they are tagged.
+// Tile q's word is words[q & mask] and carries tag base_tag + (q >> shift).
+// A plain launch uses one word per tile (mask = all ones, shift = 63) and the
+// launch tag; the persistent batched launch reuses a ring of 2^shift words,
+// cleared at the start of the launch, and tags each pass over the ring with
+// its generation so that a word left by tile q - 2^shift never reads as
+// tile q's.
+struct StatusRing {
+    uint64_t *words;
+    uint64_t mask;
+    uint32_t shift;
+    uint32_t base_tag;
+    __device__ __forceinline__ uint64_t *slot(uint64_t q) const { return words + (q & mask); }
+    __device__ __forceinline__ uint32_t tag(uint64_t q) const
+    {
+        return base_tag + static_cast<uint32_t>(q >> shift);
+    }
+};
+
+// Decoupled look-back by one warp: the exclusive prefix of tile `tile` over
+// the tiles first .. tile-1.  Each pass reads the 32 nearest predecessors,
+// waits until all of them are published, sums back to the nearest inclusive
+// prefix and stops there, else adds all 32 aggregates and moves on.  A wait
+// is bounded: after timeout_ns without progress `ok` is cleared and the
+// partial sum is returned.
+__device__ __forceinline__ uint32_t lookback(const StatusRing &ring, uint64_t tile, uint64_t first,
+                                             uint64_t timeout_ns, bool &ok)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t exclusive = 0;
+    int64_t pred = static_cast<int64_t>(tile) - 1;
+    uint64_t wait_start = 0;
+    bool waiting = false;
+    uint32_t backoff = 0;
+    uint32_t spins = 0;
+    ok = true;
+    while (true) {
+        const int64_t idx = pred - static_cast<int64_t>(lane);
+        bool ready = true;
+        uint64_t s = status_word(0u, true, 0u);  // before the first tile: prefix 0
+        if (idx >= static_cast<int64_t>(first)) {
+            const uint64_t q = static_cast<uint64_t>(idx);
+            s = ld_relaxed_gpu(ring.slot(q));
+            ready = static_cast<uint32_t>(s >> 33) == ring.tag(q);
+        }
+        if (__all_sync(kFull, ready)) {
+            const uint32_t incl = __ballot_sync(kFull, static_cast<uint32_t>(s >> 32) & 1u);
+            uint32_t v = static_cast<uint32_t>(s);
+            if (incl != 0u && static_cast<int>(lane) > __ffs(incl) - 1) v = 0u;
+            exclusive += __reduce_add_sync(kFull, v);
+            if (incl != 0u) break;
+            pred -= 32;
+            waiting = false;
+            backoff = 0;
+            continue;
+        }
+        uint64_t now = 0;
+        if (lane == 0) now = global_ns();
+        now = __shfl_sync(kFull, now, 0);
+        if (!waiting) {
+            waiting = true;
+            wait_start = now;
+        } else if (now - wait_start > timeout_ns || ++spins > (1u << 26)) {
+            ok = false;
+            break;
+        }
+        __nanosleep(32u << (backoff < 5u ? backoff : 5u));
+        ++backoff;
+    }
+    return exclusive;
+}
+
+// Shared state of one tile.
+template <int ENTRIES>
+struct TileShared {
+    uint32_t counts[ENTRIES];  // per (item, warp) keep counts, then their exclusive offsets
+    uint32_t tile;             // this CTA's tile ticket
+    uint32_t tag;              // launch tag
+    uint32_t prefix;           // exclusive prefix of the tile over all earlier tiles
+    uint32_t aggregate;        // kept elements in the tile
+    uint32_t ok;               // look-back finished in time
+};
+
+// Run by one full warp after every warp has written its counts: exclusive
+// scan of the ENTRIES counts in place, publication of the tile aggregate,
+// look-back, publication of the inclusive prefix.  Publishing is skipped for
+// the tile `skip_tile` (test hook).
+template <int ENTRIES>
+__device__ __forceinline__ void tile_scan_lookback(TileShared<ENTRIES> &st, const StatusRing &ring, uint64_t tile,
+                                                   uint64_t first, uint64_t timeout_ns, int64_t skip_tile,
+                                                   WsHeader *ws)
+{
+    constexpr int C = (ENTRIES + 31) / 32;
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t local[C];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int e = static_cast<int>(lane) * C + c;
+        local[c] = e < ENTRIES ? st.counts[e] : 0u;
+        sum += local[c];
+    }
+    const uint32_t incl = warp_inclusive_scan(sum);
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int e = static_cast<int>(lane) * C + c;
+        if (e < ENTRIES) st.counts[e] = run;
+        run += local[c];
+    }
+    const uint32_t aggregate = __shfl_sync(kFull, incl, 31);
+    const bool publish = static_cast<int64_t>(tile) != skip_tile;
+    const uint32_t tag = ring.tag(tile);
+    if (lane == 0 && publish) st_relaxed_gpu(ring.slot(tile), status_word(tag, tile == first, aggregate));
+    uint32_t exclusive = 0;
+    bool ok = true;
+    if (tile > first) {
+        exclusive = lookback(ring, tile, first, timeout_ns, ok);
+        if (lane == 0 && publish) st_relaxed_gpu(ring.slot(tile), status_word(tag, true, exclusive + aggregate));
+        if (lane == 0 && !ok) record_error(ws, kErrLookbackTimeout, tile);
+    }
+    if (lane == 0) {
+        st.prefix = exclusive;
+        st.aggregate = aggregate;
+        st.ok = ok ? 1u : 0u;
+    }
+}
+
+// Called by one thread per CTA once the CTA no longer reads the header: the
+// last CTA of the launch resets the ticket and the counter and advances the
+// tag, leaving the header ready for the next launch on the stream.
+__device__ __forceinline__ void finish_launch(WsHeader *ws, uint32_t tag, uint32_t ctas)
+{
+    __threadfence();
+    const uint32_t d = atomicAdd(&ws->done, 1u);
+    if (d == ctas - 1u) {
+        atomicExch(&ws->ticket, 0u);
+        atomicExch(&ws->done, 0u);
+        atomicExch(&ws->tag, next_tag(tag));
+        __threadfence();
+    }
+}
+
+}  // namespace dev
+}  // namespace bsh

@@ -1,0 +1,108 @@
+// Internal declarations shared by the C-ABI translation unit and the kernel
+// translation units of libbshuffle.  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bsh {
+
+constexpr uint32_t kMaxRounds = 64;
+
+// Device-resident header of a workspace.  One launch at a time uses it
+// (stream order).  The last CTA of every launch resets `ticket` and `done`
+// and advances `tag`, so no per-call memset is needed and a launch replayed
+// from a CUDA graph sees a clean header.
+struct WsHeader {
+    uint32_t ticket;      // next tile ticket of the running launch
+    uint32_t done;        // CTAs of the running launch that have finished
+    uint32_t tag;         // tile-status tag of the running launch, 1 .. 2^31-1
+    int32_t error;        // first device-side error code, 0 = none
+    uint64_t error_info;  // detail of that error (tile index or slot)
+    uint32_t batch_ticket;  // ticket of the persistent batched kernel
+    uint32_t batch_done;    // finished CTAs of the persistent batched kernel
+};
+
+// Shape of one shuffle: n kept slots out of a 2^k domain whose indices are
+// split into a left half of L = floor(k/2) bits and a right half of
+// R = ceil(k/2) bits (Sec. 3.2).
+struct Geometry {
+    uint32_t n;       // number of kept slots, n <= 2^32 - 1
+    uint32_t k;       // domain exponent, 4 <= k <= 32
+    uint32_t L, R;    // half widths
+    uint32_t lmask;   // 2^L - 1
+    uint32_t rmask;   // 2^R - 1
+    uint64_t domain;  // 2^k
+};
+
+// Everything one fused tile launch needs, passed by value (param space).
+struct TileArgs {
+    const void *in;
+    void *out;
+    Geometry g;
+    uint32_t rounds;
+    uint32_t num_tiles;
+    uint32_t elem_bytes;        // element width for the row kernels
+    uint32_t pad0;
+    int64_t skip_publish_tile;  // test hook, -1 = off
+    uint64_t timeout_ns;        // look-back wait limit
+    WsHeader *ws;
+    uint64_t *status;           // one word per tile
+    uint32_t keys[kMaxRounds];
+};
+
+// What a fused launch writes.
+enum class Mode : int {
+    Gather = 0,   // out[j] = in[f(i_j)]            (bshuffle_permute)
+    Scatter = 1,  // out[f(i_j)] = in[j]            (bshuffle_inverse)
+    Index32 = 2,  // out[j] = (uint32) f(i_j)       (bshuffle_indices)
+    Index64 = 3,  // out[j] = (uint64) f(i_j)
+};
+
+// Domain indices per tile of the element kernels and of the row kernels.
+uint32_t elem_tile_size(uint32_t elem_bytes, Mode mode);
+uint32_t rows_tile_size();
+
+// Enqueue one fused launch of num_tiles CTAs.  elem_bytes selects the
+// element kernel (1, 2, 4, 8, 16) or the row kernel (multiple of 16, > 16).
+cudaError_t launch_elem(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream);
+cudaError_t launch_rows(const TileArgs &a, Mode mode, cudaStream_t stream);
+
+// ------------------------------------------------------------------ batched
+
+// Device-side descriptor, layout identical to the public bshuffle_desc.
+struct BatchDesc {
+    const void *in;
+    void *out;
+    uint64_t n;
+    uint64_t seed;
+};
+
+// Per-instance plan written by the planning kernel.
+struct BatchPlan {
+    uint64_t first_tile;  // global index of the instance's first tile
+    uint32_t k;           // domain exponent (0 for an empty instance)
+    uint32_t tiles;       // tiles of the instance
+};
+
+struct BatchArgs {
+    const BatchDesc *descs;
+    BatchPlan *plan;        // count entries
+    uint64_t *tile_prefix;  // count + 1 entries: exclusive scan of tile counts, then the total
+    uint32_t count;
+    uint32_t rounds;
+    uint32_t elem_bytes;
+    uint32_t grid;          // CTAs of the persistent kernel
+    uint64_t timeout_ns;
+    int64_t skip_publish_tile;
+    WsHeader *ws;
+    uint64_t *status;       // look-back ring of batch_ring_words() words
+    uint64_t *total_tiles;  // written by the planning kernel
+};
+
+uint32_t batch_tile_size(uint32_t elem_bytes);
+uint64_t batch_ring_words();
+// Enqueue the planning kernel and the persistent kernel (elem_bytes 1..16).
+cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream);
+
+}  // namespace bsh

@@ -1,0 +1,292 @@
+// Many independent shuffles in one persistent launch.
+//
+// Every instance t (its own input, output, length n_t and seed) is cut into
+// tiles of the same size as the plain element kernel's.  The tiles of all
+// instances form one global sequence, instance after instance, handed out by
+// a global ticket to a grid of persistent CTAs (a few per SM).  A CTA maps its
+// ticket to (instance, tile) by a warp-cooperative search of the tile prefix
+// table, derives the instance's round keys from its seed, and runs the same
+// fused pipeline as the plain kernel: bijection, gather, in-tile scan, and a
+// decoupled look-back that stops at the instance's first tile.  The output of
+// each instance is exactly that of a plain call with the same arguments.
+//
+// A small planning kernel (one CTA) runs first: it validates the descriptors,
+// computes every instance's domain exponent and tile count, scans the tile
+// counts, and clears the status ring used by the look-back.
+#include <cstdint>
+
+#include "bshuffle_device.cuh"
+#include "bshuffle_internal.h"
+
+namespace bsh {
+namespace {
+
+using dev::kFull;
+
+constexpr int kBBlock = 256;
+constexpr int kBItems = 8;
+constexpr uint32_t kTile = kBBlock * kBItems;
+constexpr uint32_t kRingShift = 16;
+constexpr uint64_t kRingWords = uint64_t{1} << kRingShift;
+constexpr int kPlanThreads = 1024;
+constexpr int kErrInvalid = -10;
+constexpr int kErrAlign = -6;
+
+__device__ __forceinline__ uint32_t domain_bits_dev(uint64_t n)
+{
+    if (n == 0) return 0;
+    const uint32_t k = 64u - static_cast<uint32_t>(__clzll(n - 1));  // ceil(log2 n) for n >= 2
+    return n == 1 ? 4u : (k < 4u ? 4u : k);
+}
+
+__global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const __grid_constant__ BatchArgs a)
+{
+    __shared__ uint64_t s_sums[kPlanThreads];
+    const uint32_t tid = threadIdx.x;
+    for (uint64_t w = tid; w < kRingWords; w += kPlanThreads) a.status[w] = 0ull;
+
+    const uint32_t per = (a.count + kPlanThreads - 1) / kPlanThreads;
+    const uint32_t begin = tid * per;
+    const uint32_t end = begin + per < a.count ? begin + per : a.count;
+    uint64_t sum = 0;
+    for (uint32_t t = begin; t < end; ++t) {
+        const BatchDesc d = a.descs[t];
+        uint32_t k = domain_bits_dev(d.n);
+        bool bad = false;
+        if (d.n > 4294967295ull) {
+            dev::record_error(a.ws, kErrInvalid, t);
+            bad = true;
+        } else if (d.n > 0 && (d.in == nullptr || d.out == nullptr)) {
+            dev::record_error(a.ws, kErrInvalid, t);
+            bad = true;
+        } else if (d.n > 0) {
+            const uint64_t al = a.elem_bytes < 16u ? a.elem_bytes : 16u;
+            if (reinterpret_cast<uintptr_t>(d.in) % al != 0 || reinterpret_cast<uintptr_t>(d.out) % al != 0) {
+                dev::record_error(a.ws, kErrAlign, t);
+                bad = true;
+            }
+        }
+        if (bad) k = 0;
+        const uint64_t tiles = k == 0 ? 0 : ((uint64_t{1} << k) + kTile - 1) / kTile;
+        a.plan[t].k = k;
+        a.plan[t].tiles = static_cast<uint32_t>(tiles);
+        sum += tiles;
+    }
+    s_sums[tid] = sum;
+    __syncthreads();
+    // exclusive scan of the per-thread sums (Hillis-Steele over 1024 entries)
+    for (int d = 1; d < kPlanThreads; d <<= 1) {
+        const uint64_t v = tid >= static_cast<uint32_t>(d) ? s_sums[tid - d] : 0ull;
+        __syncthreads();
+        s_sums[tid] += v;
+        __syncthreads();
+    }
+    uint64_t run = s_sums[tid] - sum;
+    for (uint32_t t = begin; t < end; ++t) {
+        a.plan[t].first_tile = run;
+        a.tile_prefix[t] = run;
+        run += a.plan[t].tiles;
+    }
+    if (tid == kPlanThreads - 1) {
+        uint64_t total = s_sums[tid];
+        if (total > 0xfff00000ull) {  // tickets are 32-bit
+            dev::record_error(a.ws, kErrInvalid, total);
+            total = 0;
+        }
+        a.tile_prefix[a.count] = total;
+        *a.total_tiles = total;
+    }
+}
+
+// The instance owning global tile g: the largest t with tile_prefix[t] <= g.
+// Warp-cooperative: every pass splits the candidate range into 32 parts.
+__device__ __forceinline__ uint32_t find_instance(const uint64_t *prefix, uint32_t count, uint64_t g)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t lo = 0, hi = count;  // answer in [lo, hi)
+    while (hi - lo > 32u) {
+        const uint32_t span = hi - lo;
+        const uint32_t m = lo + static_cast<uint32_t>((static_cast<uint64_t>(span) * lane) / 32u);
+        const bool le = prefix[m] <= g;
+        const uint32_t ball = __ballot_sync(kFull, le);
+        const int top = 31 - __clz(ball);  // lane 0 always qualifies (prefix[lo] <= g)
+        const uint32_t new_lo = lo + static_cast<uint32_t>((static_cast<uint64_t>(span) * top) / 32u);
+        const uint32_t new_hi = top == 31 ? hi : lo + static_cast<uint32_t>((static_cast<uint64_t>(span) * (top + 1)) / 32u);
+        lo = new_lo;
+        hi = new_hi;
+    }
+    const uint32_t m = lo + lane;
+    const bool le = m < hi && prefix[m] <= g;
+    const uint32_t ball = __ballot_sync(kFull, le);
+    return lo + static_cast<uint32_t>(31 - __clz(ball));
+}
+
+__device__ __forceinline__ uint32_t splitmix_key(uint64_t seed, uint32_t r)
+{
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (static_cast<uint64_t>(r) + 1ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return static_cast<uint32_t>(z ^ (z >> 31));
+}
+
+struct BatchJob {
+    const void *in;
+    void *out;
+    uint64_t first;
+    Geometry g;
+    uint64_t ticket;
+};
+
+template <class T, bool ODD, int ITEMS>
+__device__ __forceinline__ void batch_tile(const BatchArgs &a, const BatchJob &job, const uint32_t *keys,
+                                           dev::TileShared<ITEMS *(kBBlock / 32)> &st, const dev::StatusRing &ring)
+{
+    constexpr int WARPS = kBBlock / 32;
+    constexpr int ENTRIES = ITEMS * WARPS;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    const Geometry &g = job.g;
+    const uint64_t tile = job.ticket;
+    const uint32_t base = static_cast<uint32_t>(tile - job.first) * kTile;
+
+    uint32_t left[ITEMS], right[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t i = base + static_cast<uint32_t>(j * kBBlock) + threadIdx.x;
+        left[j] = i >> g.R;
+        right[j] = i & g.rmask;
+    }
+    dev::cipher_items<ODD, ITEMS>(left, right, keys, a.rounds, g);
+    uint32_t src[ITEMS];
+    bool keep[ITEMS];
+    T val[ITEMS];
+    const T *in = static_cast<const T *>(job.in);
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t i = base + static_cast<uint32_t>(j * kBBlock) + threadIdx.x;
+        src[j] = (left[j] << g.R) | right[j];
+        keep[j] = static_cast<uint64_t>(i) < g.domain && src[j] < g.n;
+        if (keep[j]) val[j] = __ldg(in + src[j]);
+    }
+    uint32_t mask[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) mask[j] = __ballot_sync(kFull, keep[j]);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) st.counts[j * WARPS + warp] = __popc(mask[j]);
+    }
+    __syncthreads();
+    if (warp == 0)
+        dev::tile_scan_lookback<ENTRIES>(st, ring, tile, job.first, a.timeout_ns, a.skip_publish_tile, a.ws);
+    __syncthreads();
+    if (st.ok != 0u) {
+        const uint32_t prefix = st.prefix;
+        const uint32_t lt = dev::lanemask_lt();
+        T *out = static_cast<T *>(job.out);
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t dst = prefix + st.counts[j * WARPS + warp] + __popc(mask[j] & lt);
+            if (keep[j]) {
+                if (dst < g.n) out[dst] = val[j];
+                else dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
+            }
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBBlock) batch_tile_kernel(const __grid_constant__ BatchArgs a)
+{
+    constexpr int ENTRIES = kBItems * (kBBlock / 32);
+    __shared__ dev::TileShared<ENTRIES> st;
+    __shared__ uint32_t s_keys[kMaxRounds];
+    __shared__ BatchJob s_job;
+    const dev::StatusRing ring{a.status, kRingWords - 1, kRingShift, 1u};
+    const uint64_t total = *reinterpret_cast<volatile const uint64_t *>(a.total_tiles);
+
+    while (true) {
+        if (threadIdx.x == 0) s_job.ticket = atomicAdd(&a.ws->batch_ticket, 1u);
+        __syncthreads();
+        const uint64_t ticket = s_job.ticket;
+        if (ticket >= total) break;
+        if (threadIdx.x < 32) {
+            const uint32_t t = find_instance(a.tile_prefix, a.count, ticket);
+            if (threadIdx.x == 0) {
+                const BatchDesc d = a.descs[t];
+                const uint32_t k = a.plan[t].k;
+                s_job.in = d.in;
+                s_job.out = d.out;
+                s_job.first = a.plan[t].first_tile;
+                s_job.g.n = static_cast<uint32_t>(d.n);
+                s_job.g.k = k;
+                s_job.g.L = k / 2;
+                s_job.g.R = k - k / 2;
+                s_job.g.lmask = (1u << (k / 2)) - 1u;
+                s_job.g.rmask = (k - k / 2) >= 32 ? 0xffffffffu : ((1u << (k - k / 2)) - 1u);
+                s_job.g.domain = uint64_t{1} << k;
+            }
+            const uint64_t seed = __shfl_sync(kFull, threadIdx.x == 0 ? a.descs[t].seed : 0ull, 0);
+            for (uint32_t r = threadIdx.x; r < a.rounds; r += 32) s_keys[r] = splitmix_key(seed, r);
+        }
+        __syncthreads();
+        const BatchJob job = s_job;
+        if (job.g.k & 1u)
+            batch_tile<T, true, kBItems>(a, job, s_keys, st, ring);
+        else
+            batch_tile<T, false, kBItems>(a, job, s_keys, st, ring);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t d = atomicAdd(&a.ws->batch_done, 1u);
+        if (d == gridDim.x - 1u) {
+            atomicExch(&a.ws->batch_ticket, 0u);
+            atomicExch(&a.ws->batch_done, 0u);
+            __threadfence();
+        }
+    }
+}
+
+template <class T>
+cudaError_t launch_typed(const BatchArgs &a, cudaStream_t stream)
+{
+    static int per_sm[64] = {0};
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (per_sm[device] == 0) {
+        int blocks = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_tile_kernel<T>, kBBlock, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return e;
+        per_sm[device] = (blocks > 0 ? blocks : 1) * sms;
+    }
+    BatchArgs b = a;
+    b.grid = static_cast<uint32_t>(per_sm[device]);
+    batch_plan_kernel<<<1, kPlanThreads, 0, stream>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_tile_kernel<T><<<b.grid, kBBlock, 0, stream>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t batch_tile_size(uint32_t) { return kTile; }
+uint64_t batch_ring_words() { return kRingWords; }
+
+cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream)
+{
+    switch (a.elem_bytes) {
+    case 1: return launch_typed<unsigned char>(a, stream);
+    case 2: return launch_typed<unsigned short>(a, stream);
+    case 4: return launch_typed<unsigned int>(a, stream);
+    case 8: return launch_typed<unsigned long long>(a, stream);
+    case 16: return launch_typed<uint4>(a, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bsh

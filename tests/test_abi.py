@@ -1,0 +1,116 @@
+"""The C-ABI library on the CPU: it loads, exports every function that
+include/bshuffle.h declares, its host-side arithmetic (domain exponent, key
+schedule) agrees with the oracle, and argument errors are reported before any
+CUDA call.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bshuffle.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_06161_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bshuffle_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("bshuffle_permute", "bshuffle_indices", "bshuffle_inverse", "bshuffle_batched",
+                     "bshuffle_get_error", "bshuffle_error_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2106_06161_gb300 import _lib
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+
+
+def test_exports_are_c_symbols():
+    from paper_2106_06161_gb300 import _lib, build
+    path = build.build()
+    syms = ctypes.CDLL(path)
+    for name in _declared_functions():
+        ctypes.cast(getattr(syms, name), ctypes.c_void_p)  # resolvable without C++ mangling
+    assert os.path.dirname(path).startswith(os.path.join(ROOT, "paper_2106_06161_gb300"))
+    assert _lib.LIB_PATH == path
+
+
+def test_domain_bits_agree_with_oracle(lib):
+    from paper_2106_06161_gb300 import bshuffle_domain_bits
+    for n in [1, 2, 5, 16, 17, 1000, 65536, 65537, 1_000_003, 2**28, 2**28 + 12345, 2**32 - 1]:
+        assert bshuffle_domain_bits(n) == oracle.domain_bits(n), n
+
+
+def test_round_keys_agree_with_oracle(lib):
+    from paper_2106_06161_gb300 import bshuffle_round_keys
+    for seed in [0, 1, 42, 2**63 + 5, 2**64 - 1]:
+        for rounds in [0, 1, 24, 64]:
+            assert bshuffle_round_keys(seed, rounds) == oracle.round_keys(seed, rounds).tolist()
+
+
+def test_error_strings(lib):
+    from paper_2106_06161_gb300 import error_string
+    for code in range(0, -11, -1):
+        s = error_string(code)
+        assert s and "unknown" not in s
+    assert "unknown" in error_string(-1234)
+
+
+def test_argument_errors_precede_cuda(lib):
+    from paper_2106_06161_gb300 import _lib as L
+    buf = (ctypes.c_uint64 * 64)()
+    a = ctypes.addressof(buf)
+    p = lib.bshuffle_permute
+    assert p(a, a + 256, 4, 8, 0, 65, None) == L.BSHUFFLE_ERR_ROUNDS
+    assert p(a, a + 256, 4, 3, 0, 24, None) == L.BSHUFFLE_ERR_ELEM
+    assert p(a, a + 256, 4, 24, 0, 24, None) == L.BSHUFFLE_ERR_ELEM
+    assert p(None, a + 256, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_NULL
+    assert p(a, a + 16, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_ALIAS
+    assert p(a + 4, a + 256, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_ALIGN
+    assert p(a, a + 256, 2**32, 1, 0, 24, None) == L.BSHUFFLE_ERR_TOO_LARGE
+    assert p(a, a + 256, 0, 8, 0, 24, None) == L.BSHUFFLE_OK       # empty: no-op
+    assert lib.bshuffle_inverse(a, a + 8, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_ALIAS
+    assert lib.bshuffle_indices(a, 2, 4, 0, 24, None) == L.BSHUFFLE_ERR_ELEM
+    assert lib.bshuffle_indices(None, 4, 4, 0, 24, None) == L.BSHUFFLE_ERR_NULL
+    assert lib.bshuffle_indices(a + 2, 4, 4, 0, 24, None) == L.BSHUFFLE_ERR_ALIGN
+    assert lib.bshuffle_batched(None, 0, 8, 24, None) == L.BSHUFFLE_OK
+    assert lib.bshuffle_batched(None, 3, 8, 24, None) == L.BSHUFFLE_ERR_NULL
+    assert lib.bshuffle_batched(a, 3, 8, 99, None) == L.BSHUFFLE_ERR_ROUNDS
+
+
+def test_no_device_means_cuda_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2106_06161_gb300 import _lib as L
+    buf = (ctypes.c_uint64 * 64)()
+    a = ctypes.addressof(buf)
+    assert lib.bshuffle_permute(a, a + 256, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_CUDA
+
+
+def test_binding_has_no_cpu_fallback():
+    # The product package must not reach the oracle or any CPU shuffle.
+    pkg = os.path.join(ROOT, "paper_2106_06161_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "bshuffle_oracle" not in text, f

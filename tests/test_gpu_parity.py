@@ -1,0 +1,210 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything the library computes is integer index arithmetic and byte moves,
+so the bar is bit-exact equality for every width.  Small and mid sizes are
+compared element by element; the full-size sweep points are compared against
+one full oracle pass (2^28 + 12345) or against the oracle evaluated at sampled
+slots (2^28, no dropped indices), plus properties that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from tests.gpu_helpers import assert_no_device_error, to_device, to_host
+
+pytestmark = pytest.mark.gpu
+
+bs = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    global bs
+    from paper_2106_06161_gb300 import build
+    build.build()
+    import paper_2106_06161_gb300
+    bs = paper_2106_06161_gb300
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    bs.load()
+    yield
+
+
+def gpu_permute(x: np.ndarray, seed: int, rounds: int = 24) -> np.ndarray:
+    y = bs.permute(to_device(x), seed, rounds)
+    assert_no_device_error()
+    return to_host(y, x)
+
+
+def gpu_inverse(x: np.ndarray, seed: int, rounds: int = 24) -> np.ndarray:
+    y = bs.inverse(to_device(x), seed, rounds)
+    assert_no_device_error()
+    return to_host(y, x)
+
+
+SMALL_N = [1, 2, 3, 5, 15, 16, 17, 31, 100, 1000, 2047, 2048, 2049, 4095, 4097, 65535, 65537, 123457]
+
+
+def _payload(n: int, width: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed * 1000 + width)
+    if width in (1, 2, 4, 8):
+        dt = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[width]
+        return rng.integers(0, np.iinfo(dt).max, size=n, dtype=dt, endpoint=True)
+    return rng.integers(0, 256, size=(n, width), dtype=np.uint8)
+
+
+def test_single_shuffle_config():
+    # n = 1,000,003 uint32 iota, seed 42, domain 2^20, 24 rounds
+    n = workloads.SINGLE_N
+    assert bs.domain_bits(n) == 20
+    x = workloads.iota(n, np.uint32)
+    y = gpu_permute(x, workloads.SINGLE_SEED)
+    want = oracle.permute(x, workloads.SINGLE_SEED)
+    assert np.array_equal(y, want)
+    assert np.array_equal(np.sort(y), x)  # a permutation
+
+
+@pytest.mark.parametrize("width", [1, 2, 4, 8, 16, 32, 48, 4096])
+def test_permute_matches_oracle_all_widths(width):
+    for n in SMALL_N:
+        if width >= 48 and n > 20000:
+            continue
+        for seed in (0, 7):
+            x = _payload(n, width, seed)
+            assert np.array_equal(gpu_permute(x, seed), oracle.permute(x, seed)), (n, seed)
+
+
+@pytest.mark.parametrize("rounds", [0, 1, 2, 23, 24, 64])
+def test_permute_rounds(rounds):
+    for n in (17, 4097, 100003):
+        x = _payload(n, 8, rounds)
+        assert np.array_equal(gpu_permute(x, 11, rounds), oracle.permute(x, 11, rounds))
+
+
+@pytest.mark.parametrize("idx_dtype", [torch.int32, torch.int64])
+def test_indices_match_oracle(idx_dtype):
+    for n in SMALL_N + [2**20 + 1]:
+        idx = bs.indices(n, 5, dtype=idx_dtype)
+        assert_no_device_error()
+        assert np.array_equal(idx.cpu().numpy().astype(np.uint64), oracle.indices(n, 5)), n
+
+
+@pytest.mark.parametrize("width", [1, 4, 8, 16, 64])
+def test_inverse_matches_oracle(width):
+    for n in (1, 3, 17, 2049, 65537):
+        x = _payload(n, width, 3)
+        y = gpu_inverse(x, 9)
+        assert np.array_equal(y, oracle.inverse(x, 9)), n
+        assert np.array_equal(gpu_inverse(gpu_permute(x, 9), 9), x)
+
+
+def test_unaligned_heads_and_views():
+    # output/input starting inside a 16-byte line, and a strided source
+    for width, dt in ((4, torch.int32), (8, torch.int64)):
+        n = 70001
+        base = torch.arange(n + 3, dtype=dt, device="cuda")
+        x = base[1:n + 1]
+        out = torch.empty(n + 3, dtype=dt, device="cuda")[3:]
+        bs.permute(x, 123, out=out)
+        assert_no_device_error()
+        want = oracle.permute(np.arange(1, n + 1, dtype=np.int64).astype(np.uint64 if width == 8 else np.uint32), 123)
+        assert np.array_equal(out.cpu().numpy().astype(np.uint64), want.astype(np.uint64))
+    m = torch.arange(4000, dtype=torch.int64, device="cuda").reshape(1000, 4)[:, 1]  # non-contiguous
+    y = bs.permute(m, 2)
+    assert np.array_equal(y.cpu().numpy(), oracle.permute(m.cpu().numpy(), 2))
+
+
+def test_empty_input_is_a_noop():
+    x = torch.empty(0, dtype=torch.int64, device="cuda")
+    assert bs.permute(x, 1).numel() == 0
+    assert bs.indices(0, 1).numel() == 0
+    assert_no_device_error()
+
+
+@pytest.mark.parametrize("width", [4, 8, 16])
+def test_sweep_sizes_up_to_2_24(width):
+    for n in (2**10, 2**16, 2**20, 2**24):
+        for seed in workloads.SWEEP_SEEDS:
+            if n == 2**24 and seed > 1:
+                continue
+            x = workloads.sweep_payload(n, width, seed)
+            assert np.array_equal(gpu_permute(x, seed), oracle.permute(x, seed)), (n, seed)
+
+
+def _window_check(idx: np.ndarray, n: int, seed: int, starts):
+    """Consecutive slots must come from increasing domain indices with every
+    index in between dropped (its image is >= n)."""
+    k = oracle.domain_bits(n)
+    keys = oracle.round_keys(seed, 24)
+    for j0 in starts:
+        win = idx[j0:j0 + 256].astype(np.uint64)
+        pre = oracle.varphilox_inverse(win, k, keys)
+        assert np.all(np.diff(pre.astype(np.int64)) > 0)
+        between = np.setdiff1d(np.arange(int(pre[0]), int(pre[-1]) + 1, dtype=np.uint64), pre)
+        assert np.all(oracle.varphilox(between, k, keys) >= n)
+
+
+def test_full_size_power_of_two_u64_sampled():
+    # n = 2^28 uint64: no index is dropped, so slot j holds X[f(j)].
+    n, seed = 2**28, 0
+    x = workloads.uniform_u64(n, seed)
+    xd = to_device(x)
+    y = bs.permute(xd, seed)
+    assert_no_device_error()
+    rng = np.random.default_rng(1)
+    js = np.concatenate([np.arange(4096), rng.integers(0, n, 200_000), np.arange(n - 4096, n)]).astype(np.uint64)
+    src = oracle.varphilox(js, 28, oracle.round_keys(seed, 24))
+    got = y[torch.from_numpy(js.astype(np.int64)).cuda()].cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, x[src.astype(np.int64)])
+    # any size: the output is a permutation of the input
+    assert torch.equal(torch.sort(y).values, torch.sort(xd).values)
+
+
+def test_full_size_worst_case_padding_exact():
+    # n = 2^28 + 12345 (domain 2^29, about half the images dropped): one full
+    # oracle pass, compared slot for slot with the GPU's indices and payload.
+    n, seed = 2**28 + 12345, 0
+    want = oracle.indices(n, seed)
+    idx = bs.indices(n, seed, dtype=torch.int64)
+    assert_no_device_error()
+    assert np.array_equal(idx.cpu().numpy().view(np.uint64), want)
+    x = workloads.uniform_u64(n, seed)
+    y = bs.permute(to_device(x), seed)
+    assert_no_device_error()
+    rng = np.random.default_rng(2)
+    js = np.concatenate([np.arange(2048), rng.integers(0, n, 300_000), np.arange(n - 2048, n)])
+    got = y[torch.from_numpy(js).cuda()].cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, x[want[js].astype(np.int64)])
+
+
+def test_full_size_other_seeds_properties():
+    n = 2**28 + 12345
+    for seed in (1, 4):
+        idx = bs.indices(n, seed, dtype=torch.int64)
+        assert_no_device_error()
+        counts = torch.bincount(idx, minlength=n)
+        assert int(counts.max()) == 1 and int(counts.min()) == 1
+        h = idx.cpu().numpy()
+        _window_check(h, n, seed, [0, 1 << 20, 1 << 27, n - 256])
+
+
+def test_repeated_calls_reuse_workspace():
+    # The per-stream header is reset by the last CTA of every launch.
+    x = _payload(300001, 4, 1)
+    want = oracle.permute(x, 77)
+    for _ in range(5):
+        assert np.array_equal(gpu_permute(x, 77), want)
+    # a bigger call grows the workspace, a smaller one reuses it
+    big = _payload(2**22 + 5, 4, 2)
+    assert np.array_equal(gpu_permute(big, 1), oracle.permute(big, 1))
+    assert np.array_equal(gpu_permute(x, 77), want)
+
+
+def test_other_stream():
+    x = _payload(100000, 8, 5)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        y = bs.permute(to_device(x), 4)
+        s.synchronize()
+        assert bs.get_error() == 0
+    assert np.array_equal(to_host(y, x), oracle.permute(x, 4))

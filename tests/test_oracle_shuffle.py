@@ -63,6 +63,14 @@ def test_permute_moves_whole_elements(width):
     assert np.array_equal(y, x[idx])
 
 
+def test_permute_first_is_a_prefix():
+    for n in (17, 1000, 70001):
+        x = workloads.uniform_u64(n, 3)
+        full = oracle.permute(x, 8)
+        for slots in (1, 5, n // 2, n):
+            assert np.array_equal(oracle.permute_first(x, 8, slots), full[:slots])
+
+
 def test_inverse_undoes_permute():
     for n in (1, 2, 17, 1000, 4099):
         x = workloads.uniform_u64(n, n)
