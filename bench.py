@@ -218,7 +218,7 @@ def traffic_for(fingerprint: str):
         return None
     with open(TRAFFIC_FILE) as fh:
         d = json.load(fh)
-    if d.get("library_fingerprint") != fingerprint:
+    if d.get("kernel_fingerprint") != fingerprint:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -267,7 +267,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     algo_bytes = 2 * N_MAIN * ELEM
     achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
-    fp = open(os.path.join(bsbuild.BUILD_DIR, "stamp.txt")).read().strip()
+    fp = bsbuild.kernel_fingerprint("kernels_elem.cu")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_for(fp), "peak_kind": peak_kind,
                 "kernel": "elem_tile_kernel<uint64, Gather, even k>",

@@ -49,8 +49,19 @@ def _fingerprint(sources: list[str]) -> str:
         h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + [f for f in NVCC_FLAGS if not os.path.isabs(f)]).encode())
     return h.hexdigest()
+
+
+def kernel_fingerprint(source: str) -> str:
+    """Hash of one kernel translation unit, the headers it includes and the flags."""
+    h = hashlib.sha256()
+    for name in (source, "bshuffle_device.cuh", "bshuffle_internal.h"):
+        h.update(name.encode())
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(ARCH + [f for f in NVCC_FLAGS if not os.path.isabs(f)]).encode())
+    return h.hexdigest()[:16]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
