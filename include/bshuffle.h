@@ -179,6 +179,38 @@ int bshuffle_set_lookback_timeout_ns(uint64_t ns);
  */
 int bshuffle_debug_skip_publish(int64_t tile);
 
+/*
+ * Allocation-free variant of bshuffle_permute, for callers that cannot
+ * allocate device memory when they call: a process that has reserved all of
+ * the device's memory for its own pool (cudaMalloc would fail), or a
+ * latency-critical loop that cannot take the device-wide synchronisation
+ * that cudaMalloc/cudaFree may cause.  The paper has no counterpart; this is
+ * a deployment convenience.
+ *   Output.    Identical to bshuffle_permute(in, out, n, elem_bytes, seed,
+ *              rounds, stream).  The caller passes in and out as usual.
+ *   Scratch.   The tile-status words and launch counters live in one
+ *              file-scope device array of 512 KiB + 256 B that every GPU
+ *              loading the library holds until the process exits.  No call
+ *              allocates or frees device memory.
+ *   Limits.    elem_bytes 1, 2, 4, 8 or 16; n <= 2^27 (134,217,728);
+ *              larger n returns BSHUFFLE_ERR_TOO_LARGE.
+ *   Set-up.    The first call on a device looks up the array's device
+ *              address with that device current and initialises its launch
+ *              tag (one small synchronous copy); make that first call before
+ *              any stream capture.
+ *   Sharing.   Every call on a device shares the one array, which keeps the
+ *              last call's contents; each call clears the counters that must
+ *              start at zero.  Calls that overlap on the GPU (e.g. on two
+ *              streams at once) race and corrupt each other's output:
+ *              serialise them.
+ *   Errors.    Argument errors as for bshuffle_permute.  A device-side
+ *              look-back timeout is recorded in the array's own error word
+ *              and is not reported by bshuffle_get_error (which reads the
+ *              per-stream workspaces only).
+ */
+int bshuffle_permute_static(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                            uint32_t rounds, void *stream);
+
 /* Library version as major * 10000 + minor * 100 + patch. */
 int bshuffle_version(void);
 

@@ -45,6 +45,7 @@ SIGNATURES = {
     "bshuffle_set_lookback_timeout_ns": (_int, [_u64]),
     "bshuffle_debug_skip_publish": (_int, [_i64]),
     "bshuffle_version": (_int, []),
+    "bshuffle_permute_static": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
 }
 
 _lock = threading.Lock()

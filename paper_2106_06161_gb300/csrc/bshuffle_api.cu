@@ -398,3 +398,95 @@ int bshuffle_debug_skip_publish(int64_t tile)
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free entry point
+//
+// bshuffle_permute_static runs the same element kernel as bshuffle_permute,
+// but its scratch (launch counters, tag, error word and the tile-status
+// words) lives in the file-scope device array below instead of a cudaMalloc'd
+// per-stream workspace.  It is meant for callers that cannot allocate device
+// memory at call time: a process that has already reserved all device memory
+// for its own pool (so cudaMalloc would fail), or a latency-critical loop that
+// cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+// cause.
+
+namespace {
+
+constexpr uint64_t kStaticTiles = 65536;                       // tile-status words
+constexpr uint64_t kStaticMaxN = kStaticTiles * 2048;          // 2^27 elements (2048 per tile)
+constexpr size_t kStaticBytes = kHeaderBytes + kStaticTiles * sizeof(uint64_t);  // 512 KiB + 256 B
+
+// Held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void *g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, set up once per
+// device: the symbol's address is looked up with that device current (in
+// host code the array's name is only a host-side stand-in) and its launch tag
+// is set to 1, so that the zero-initialised status words never read as
+// published.
+int static_scratch(void **out)
+{
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (device < 0 || device >= kMaxDevices) return BSHUFFLE_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (g_static_addr[device] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e);
+        WsHeader h{};
+        h.tag = 1;
+        e = cudaMemcpy(p, &h, sizeof(h), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e);
+        g_static_addr[device] = p;
+    }
+    *out = g_static_addr[device];
+    return BSHUFFLE_OK;
+}
+
+}  // namespace
+
+extern "C" int bshuffle_permute_static(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                                       uint32_t rounds, void *stream_ptr)
+{
+    int rc = check_common(n, rounds);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (elem_bytes != 1 && elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16)
+        return BSHUFFLE_ERR_ELEM;
+    if (n == 0) return BSHUFFLE_OK;
+    if (n > kStaticMaxN) return BSHUFFLE_ERR_TOO_LARGE;
+    rc = check_buffers(in, out, n, elem_bytes);
+    if (rc != BSHUFFLE_OK) return rc;
+
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    TileArgs a{};
+    a.in = in;
+    a.out = out;
+    a.g = geometry_of(n);
+    a.rounds = rounds;
+    a.elem_bytes = elem_bytes;
+    a.skip_publish_tile = g_skip_publish.load();
+    a.timeout_ns = g_timeout_ns.load();
+    fill_keys(seed, rounds, a.keys);
+    const uint64_t tile = bsh::elem_tile_size(elem_bytes, Mode::Gather);
+    const uint64_t tiles = (a.g.domain + tile - 1) / tile;
+    if (tiles > kStaticTiles) return BSHUFFLE_ERR_TOO_LARGE;
+    a.num_tiles = static_cast<uint32_t>(tiles);
+
+    void *scratch = nullptr;
+    rc = static_scratch(&scratch);
+    if (rc != BSHUFFLE_OK) return rc;
+    a.ws = static_cast<WsHeader *>(scratch);
+    a.status = reinterpret_cast<uint64_t *>(static_cast<char *>(scratch) + kHeaderBytes);
+    // The tile ticket and the completion counter must start at zero; the
+    // status words carry the launch tag and need no clearing.
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = bsh::launch_elem(a, Mode::Gather, elem_bytes, stream);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
