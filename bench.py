@@ -355,6 +355,20 @@ def secondary(bs, torch, dev, stream):
         "logical_gbps": 2 * N_WORST * ELEM / (statistics.mean(per) * 1e-3) / 1e9}
     del x, y
 
+    # the paper's throughput bound: a random gather of the same size (no cipher, no scan)
+    host = workloads.uniform_u64(N_MAIN, 2)
+    x = torch.from_numpy(host.view(np.int64)).to(dev)
+    y = torch.empty_like(x)
+    xp, yp = x.data_ptr(), y.data_ptr()
+    g = lambda: bs.bshuffle_random_gather(xp, yp, N_MAIN, ELEM, sptr)  # noqa: E731
+    for _ in range(3):
+        g()
+    per, region = timed_launches(g, 20, stream, torch)
+    out["random_gather_2p28_u64"] = {
+        "elements_per_s": N_MAIN * 20 / (region * 1e-3), "launch_ms": statistics.mean(per),
+        "logical_gbps": 2 * N_MAIN * ELEM / (statistics.mean(per) * 1e-3) / 1e9}
+    del x, y
+
     # 4096 uneven instances, int32: one batched launch vs one plain launch each
     sizes = workloads.batched_sizes()
     data = torch.from_numpy(workloads.batched_payloads(sizes)).to(dev)

@@ -139,6 +139,34 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
                      void *stream);
 
 /*
+ * Permutation Monte Carlo statistic fused with the shuffle (an application
+ * named in Sec. 1; the shuffled data never leaves registers and nothing but T
+ * is written).  For b in [0, count):
+ *     y = bshuffle_permute(x, n, seed = base_seed + b, rounds)
+ *     T[b] = mean(y[0:n1]) - mean(y[n1:n])          (FP64 sums)
+ *   x       device array of n float32 values (caller-owned, read only)
+ *   n1      size of the first group, 0 < n1 < n
+ *   T       device array of count doubles (caller-owned)
+ * Slots fill in increasing domain order, so the kernel stops a shuffle once
+ * n1 elements are kept and takes the second group's sum as the total minus
+ * the first's.  Summation order differs from a sequential sum, so T agrees
+ * with it to FP64 rounding (relative differences near 1e-15), not bitwise.
+ * Needs no workspace.  Returns BSHUFFLE_ERR_INVALID unless 0 < n1 < n.
+ */
+int bshuffle_mc_group_diff(const float *x, uint64_t n, uint64_t n1, uint64_t base_seed, uint32_t count,
+                           uint32_t rounds, double *T, void *stream);
+
+/*
+ * Measurement kernel, not a shuffle API: out[i] = in[h(i)] for a fixed cheap
+ * bijection h of [0, n) (three rounds of multiply-by-odd-constant and
+ * xor-shift on k-bit values), with no cipher, keep test or scan.  It measures
+ * the random-gather bound the paper sets for every shuffle (the "Gather"
+ * column of Tables 1 and 2, Sec. 2.2).  n must be a power of two in
+ * [16, 2^32]; elem_bytes 4, 8 or 16; BSHUFFLE_ERR_INVALID otherwise.
+ */
+int bshuffle_random_gather(const void *in, void *out, uint64_t n, uint32_t elem_bytes, void *stream);
+
+/*
  * Synchronises `stream`, then returns and clears the first device-side error
  * recorded by calls on that stream since the last bshuffle_get_error:
  * BSHUFFLE_OK, BSHUFFLE_ERR_LOOKBACK_TIMEOUT or BSHUFFLE_ERR_DEVICE_BOUNDS (or

@@ -29,7 +29,9 @@ from ._lib import (
     bshuffle_get_error,
     bshuffle_indices,
     bshuffle_inverse,
+    bshuffle_mc_group_diff,
     bshuffle_permute,
+    bshuffle_random_gather,
     bshuffle_release_workspaces,
     bshuffle_round_keys,
     bshuffle_set_lookback_timeout_ns,
@@ -45,6 +47,7 @@ __all__ = [
     "bshuffle_get_error", "bshuffle_domain_bits", "bshuffle_round_keys",
     "bshuffle_release_workspaces", "bshuffle_set_lookback_timeout_ns",
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
+    "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",
 ]
 
 
@@ -191,3 +194,34 @@ def domain_bits(n: int) -> int:
 
 def round_keys(seed: int, rounds: int = DEFAULT_ROUNDS) -> list[int]:
     return bshuffle_round_keys(seed, rounds)
+
+
+def mc_group_diff(x: torch.Tensor, n1: int, base_seed: int, count: int,
+                  rounds: int = DEFAULT_ROUNDS) -> torch.Tensor:
+    """T[b] = mean(y[:n1]) - mean(y[n1:]) for y = permute(x, base_seed + b), FP64.
+
+    One fused launch; the shuffled values are never written to memory.
+    """
+    _require_cuda(x, "x")
+    if x.dtype != torch.float32 or x.dim() != 1:
+        raise ValueError("x must be a 1-D float32 CUDA tensor")
+    x = x.contiguous()
+    T = torch.empty(count, dtype=torch.float64, device=x.device)
+    bshuffle_mc_group_diff(x.data_ptr(), x.numel(), n1, base_seed, count, rounds, T.data_ptr(), _stream_of(x))
+    return T
+
+
+def mc_pvalue(x: torch.Tensor, n1: int, base_seed: int, count: int, rounds: int = DEFAULT_ROUNDS):
+    """Two-sided permutation-test p-value of the group-mean difference.
+
+    p = (1 + #{b : |T_b| >= |T_obs|}) / (count + 1), with T_obs the statistic of
+    the unshuffled sample.  Returns (p, T, T_obs).
+    """
+    T = mc_group_diff(x, n1, base_seed, count, rounds)
+    xd = x.double()
+    t_obs = float(xd[:n1].mean() - xd[n1:].mean())
+    exceed = int((T.abs() >= abs(t_obs)).sum())
+    return (1 + exceed) / (count + 1), T, t_obs
+
+
+from .autograd import BShuffleRows, shuffle_rows  # noqa: E402

@@ -46,6 +46,8 @@ SIGNATURES = {
     "bshuffle_debug_skip_publish": (_int, [_i64]),
     "bshuffle_version": (_int, []),
     "bshuffle_permute_static": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
+    "bshuffle_mc_group_diff": (_int, [_p, _u64, _u64, _u64, _u32, _u32, _p, _p]),
+    "bshuffle_random_gather": (_int, [_p, _p, _u64, _u32, _p]),
 }
 
 _lock = threading.Lock()
@@ -110,6 +112,16 @@ def bshuffle_inverse(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, seed: i
 def bshuffle_batched(descs_ptr: int, count: int, elem_bytes: int, rounds: int = DEFAULT_ROUNDS,
                      stream: int = 0) -> None:
     _check(load().bshuffle_batched(descs_ptr, count, elem_bytes, rounds, stream), "bshuffle_batched")
+
+
+def bshuffle_mc_group_diff(x_ptr: int, n: int, n1: int, base_seed: int, count: int, rounds: int,
+                           t_ptr: int, stream: int = 0) -> None:
+    _check(load().bshuffle_mc_group_diff(x_ptr, n, n1, base_seed & (2**64 - 1), count, rounds, t_ptr, stream),
+           "bshuffle_mc_group_diff")
+
+
+def bshuffle_random_gather(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, stream: int = 0) -> None:
+    _check(load().bshuffle_random_gather(in_ptr, out_ptr, n, elem_bytes, stream), "bshuffle_random_gather")
 
 
 def bshuffle_get_error(stream: int = 0) -> int:

@@ -327,6 +327,41 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 
+int bshuffle_mc_group_diff(const float *x, uint64_t n, uint64_t n1, uint64_t base_seed, uint32_t count,
+                           uint32_t rounds, double *T, void *stream)
+{
+    if (rounds > BSHUFFLE_MAX_ROUNDS) return BSHUFFLE_ERR_ROUNDS;
+    if (n > BSHUFFLE_MAX_N) return BSHUFFLE_ERR_TOO_LARGE;
+    if (count == 0) return BSHUFFLE_OK;
+    if (x == nullptr || T == nullptr) return BSHUFFLE_ERR_NULL;
+    if (n1 == 0 || n1 >= n) return BSHUFFLE_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(x) % alignof(float) != 0 || reinterpret_cast<uintptr_t>(T) % alignof(double) != 0)
+        return BSHUFFLE_ERR_ALIGN;
+    bsh::McArgs a{};
+    a.x = x;
+    a.T = T;
+    a.g = geometry_of(n);
+    a.n1 = static_cast<uint32_t>(n1);
+    a.count = count;
+    a.rounds = rounds;
+    a.base_seed = base_seed;
+    const cudaError_t e = bsh::launch_mc(a, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
+int bshuffle_random_gather(const void *in, void *out, uint64_t n, uint32_t elem_bytes, void *stream)
+{
+    if (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16) return BSHUFFLE_ERR_ELEM;
+    if (n == 0) return BSHUFFLE_OK;
+    if (n < 16 || n > (uint64_t{1} << 32) || (n & (n - 1)) != 0) return BSHUFFLE_ERR_INVALID;
+    const int rc = check_buffers(in, out, n, elem_bytes);
+    if (rc != BSHUFFLE_OK) return rc;
+    uint32_t k = 0;
+    while ((uint64_t{1} << k) < n) ++k;
+    const cudaError_t e = bsh::launch_random_gather(in, out, k, elem_bytes, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
 int bshuffle_get_error(void *stream_ptr)
 {
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);

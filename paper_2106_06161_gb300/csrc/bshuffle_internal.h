@@ -105,4 +105,24 @@ uint64_t batch_ring_words();
 // Enqueue the planning kernel and the persistent kernel (elem_bytes 1..16).
 cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream);
 
+// ------------------------------------------------------------------ Monte Carlo
+
+// Fused permutation statistic: T[b] = mean(y[:n1]) - mean(y[n1:]) of x
+// shuffled with seed base_seed + b, for b < count.
+struct McArgs {
+    const float *x;
+    double *T;
+    Geometry g;  // g.n = length of x
+    uint32_t n1;
+    uint32_t count;
+    uint32_t rounds;
+    uint32_t pad0;
+    uint64_t base_seed;
+};
+
+cudaError_t launch_mc(const McArgs &a, cudaStream_t stream);
+
+// Measurement kernel: out[i] = in[h(i)], n = 2^k, elem_bytes 4, 8 or 16.
+cudaError_t launch_random_gather(const void *in, void *out, uint32_t k, uint32_t elem_bytes, cudaStream_t stream);
+
 }  // namespace bsh

@@ -208,3 +208,27 @@ def test_other_stream():
         s.synchronize()
         assert bs.get_error() == 0
     assert np.array_equal(to_host(y, x), oracle.permute(x, 4))
+
+
+def _scramble(i: np.ndarray, k: int) -> np.ndarray:
+    """The measurement kernel's index map, restated: three rounds of
+    multiply-by-odd-constant mod 2^k then xor with the value shifted by k/2."""
+    mask = np.uint64((1 << k) - 1)
+    half = np.uint64(k // 2)
+    x = i.astype(np.uint64)
+    for c in (0x9E3779B1, 0x85EBCA77, 0xC2B2AE3D):
+        x = (x * np.uint64(c)) & mask
+        x ^= x >> half
+    return x
+
+
+@pytest.mark.parametrize("width", [4, 8, 16])
+def test_random_gather_measurement_kernel(width):
+    for k in (4, 10, 20):
+        n = 2**k
+        x = _payload(n, width, k)
+        xd = to_device(x)
+        out = torch.empty_like(xd)
+        bs.bshuffle_random_gather(xd.data_ptr(), out.data_ptr(), n, width, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(out, x), x[_scramble(np.arange(n), k).astype(np.int64)])
