@@ -46,8 +46,9 @@ N_WORST = 2**28 + 12345
 ELEM = 8
 SEED = 0
 ROUNDS = 24
-METRIC = "shuffled elements/s at n=2^28 uint64 (VariablePhilox bijective shuffle, fused single pass)"
+METRIC = "shuffled elements/s at n=2^28 uint64 (VariablePhilox bijective shuffle)"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_permute_u64_2p28.json")
+STRATEGIES = {"auto": 0, "single_pass": 1, "staged": 2}
 
 
 def parse():
@@ -57,6 +58,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
+    p.add_argument("--strategy", choices=["auto", "single_pass", "staged"], default="auto",
+                   help="how bshuffle_permute moves data (identical output)")
     p.add_argument("--profile-n", type=int, default=0,
                    help="only run warmup + steps launches of the uint64 shuffle at this n (for ncu)")
     return p.parse_args()
@@ -213,14 +216,61 @@ def timed_launches(fn, steps, stream, torch):
     return per, region0.elapsed_time(region1)
 
 
-def traffic_for(fingerprint: str):
+def traffic_for(kernel: str, fingerprint: str):
+    """DRAM bytes per launch from the committed ncu record, if the kernel is unchanged."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as fh:
         d = json.load(fh)
-    if d.get("kernel_fingerprint") != fingerprint:
+    rec = d.get("kernels", {}).get(kernel)
+    if rec is None or rec.get("kernel_fingerprint") != fingerprint:
         return None
-    return d.get("dram_bytes_per_launch")
+    return rec.get("dram_bytes_per_launch")
+
+
+# Integer issue peak of the cipher on GB300: 152 SMs x 4 schedulers x 32
+# lanes at the 2070 MHz maximum clock, over the operations one evaluation
+# needs as written (24 rounds; per even-k round the forward cipher takes two
+# product words, two XORs and one AND = 5, the inverse one more product word
+# and one more AND = 7), see DESIGN.md.
+SMS, LANES_PER_SM, SM_HZ = 152, 128, 2.07e9
+FORWARD_OPS_PER_EVAL = 24 * 5
+INVERSE_OPS_PER_EVAL = 24 * 7
+
+
+def roofline_for(passes, bsbuild):
+    """Roofline of the dominant kernel of one step, plus every pass's line."""
+    peak, peak_kind = measured_peaks()
+    n, k = N_MAIN, 28
+    if len(passes) == 1:
+        names = [("elem_tile_kernel<uint64, Gather, even k>", "kernels_elem.cu", "hbm", 2 * n * ELEM, None)]
+    else:
+        names = [("staged_bucket_kernel<uint64, even k>", "kernels_staged.cu", "alu", 2**k, n * (ELEM + ELEM + 4)),
+                 ("staged_scatter_kernel<uint64>", "kernels_staged.cu", "hbm", n * (ELEM + 4 + ELEM), None)]
+    lines = []
+    for ms, (name, src, bound, work, bytes_) in zip(passes, names):
+        if bound == "alu":
+            achieved = work / (ms * 1e-3)
+            pk = SMS * LANES_PER_SM * SM_HZ / INVERSE_OPS_PER_EVAL
+            line = {"kernel": name, "bound": "alu", "ms": ms, "achieved": achieved, "peak": pk,
+                    "unit": "inverse cipher evaluations/s", "frac": achieved / pk,
+                    "algorithmic_evals_per_launch": work,
+                    "peak_kind": "derived: 152 SMs x 128 lanes x 2.07 GHz / 168 ops per inverse evaluation",
+                    "hbm_gbs": bytes_ / (ms * 1e-3) / 1e9, "hbm_frac": bytes_ / (ms * 1e-3) / 1e9 / peak,
+                    "algorithmic_bytes_per_launch": bytes_}
+        else:
+            achieved = work / (ms * 1e-3) / 1e9
+            line = {"kernel": name, "bound": "hbm", "ms": ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "algorithmic_bytes_per_launch": work,
+                    "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+        line["traffic"] = traffic_for(name, bsbuild.kernel_fingerprint(src))
+        lines.append(line)
+    dom = max(lines, key=lambda d: d["ms"])
+    roof = {key: dom[key] for key in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roof["kernel"] = dom["kernel"]
+    roof["launch_ms"] = dom["ms"]
+    roof["peak_kind"] = dom["peak_kind"]
+    return roof, lines
 
 
 def run_ours(args):
@@ -235,6 +285,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
+    bs.bshuffle_set_strategy(STRATEGIES[args.strategy])
 
     seed = SEED + rank
     host = workloads.uniform_u64(N_MAIN, seed)
@@ -262,16 +313,18 @@ def run_ours(args):
     region_ms = max_over_ranks(region_ms, world)
     ms_per_step = region_ms / args.steps
     value = N_MAIN * world * args.steps / (region_ms * 1e-3)
-    launch_ms = statistics.mean(per)
 
-    peak, peak_kind = measured_peaks()
-    algo_bytes = 2 * N_MAIN * ELEM
-    achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
-    fp = bsbuild.kernel_fingerprint("kernels_elem.cu")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_for(fp), "peak_kind": peak_kind,
-                "kernel": "elem_tile_kernel<uint64, Gather, even k>",
-                "algorithmic_bytes_per_launch": algo_bytes}
+    # per-kernel durations, live: the same step with the library's per-pass
+    # CUDA events on this stream, read back after every step
+    bs.bshuffle_set_pass_timing(True)
+    rsteps = max(3, min(args.steps, 30))
+    pass_ms = []
+    for _ in range(rsteps):
+        step()
+        pass_ms.append(bs.bshuffle_last_pass_ms(sptr))
+    bs.bshuffle_set_pass_timing(False)
+    passes = [statistics.mean(col) for col in zip(*pass_ms)]
+    roofline, pass_lines = roofline_for(passes, bsbuild)
 
     # e2e: pinned host in -> device -> shuffle -> host out, every step
     e2e_steps = max(3, min(20, args.steps // 10))
@@ -306,6 +359,7 @@ def run_ours(args):
     extra = {}
     if not args.no_extra and rank == 0:
         extra = secondary(bs, torch, dev, stream)
+        bs.bshuffle_set_strategy(STRATEGIES[args.strategy])
 
     cpu = None
     if rank == 0 and world == 1:
@@ -327,8 +381,10 @@ def run_ours(args):
                        "n": N_MAIN, "elem_bytes": ELEM, "rounds": ROUNDS,
                        "l2": "inputs (2 GiB) larger than L2, no flush",
                        "parallelism": f"independent shuffles, {world} GPU(s)"},
-            "logical_gbps": achieved, "launch_ms": launch_ms,
-            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
+            "logical_gbps": 2 * N_MAIN * ELEM / (ms_per_step * 1e-3) / 1e9,
+            "strategy": {0: "auto", 1: "single_pass", 2: "staged"}[bs.bshuffle_get_strategy()],
+            "kernels_per_step": len(passes), "roofline": roofline, "passes": pass_lines,
+            "e2e": e2e, "gpu_launches": args.steps * len(passes), "clocks": clk,
             "cpu_baseline": cpu, "extra": extra,
         }
         print(json.dumps(line), flush=True)
@@ -341,19 +397,24 @@ def secondary(bs, torch, dev, stream):
     """Worst-case padding and the uneven batch (one-off measurements)."""
     out = {}
     sptr = stream.cuda_stream
-    # n = 2^28 + 12345: domain 2^29, about half of the images dropped
-    host = workloads.uniform_u64(N_WORST, 1)
-    x = torch.from_numpy(host.view(np.int64)).to(dev)
-    y = torch.empty_like(x)
-    xp, yp = x.data_ptr(), y.data_ptr()
-    f = lambda: bs.bshuffle_permute(xp, yp, N_WORST, ELEM, 1, ROUNDS, sptr)  # noqa: E731
-    for _ in range(3):
-        f()
-    per, region = timed_launches(f, 20, stream, torch)
-    out["worst_case_2p28_plus_12345_u64"] = {
-        "elements_per_s": N_WORST * 20 / (region * 1e-3), "launch_ms": statistics.mean(per),
-        "logical_gbps": 2 * N_WORST * ELEM / (statistics.mean(per) * 1e-3) / 1e9}
-    del x, y
+    # both strategies at n = 2^28 and at n = 2^28 + 12345 (domain 2^29, about
+    # half of the images dropped: the paper's worst case)
+    for label, n_, seed_ in (("2p28_u64", N_MAIN, 0), ("worst_case_2p28_plus_12345_u64", N_WORST, 1)):
+        host = workloads.uniform_u64(n_, seed_)
+        x = torch.from_numpy(host.view(np.int64)).to(dev)
+        y = torch.empty_like(x)
+        xp, yp = x.data_ptr(), y.data_ptr()
+        f = lambda: bs.bshuffle_permute(xp, yp, n_, ELEM, seed_, ROUNDS, sptr)  # noqa: E731
+        for name, strat in (("single_pass", bs.BSHUFFLE_STRATEGY_SINGLE_PASS), ("staged", bs.BSHUFFLE_STRATEGY_STAGED)):
+            bs.bshuffle_set_strategy(strat)
+            for _ in range(3):
+                f()
+            per, region = timed_launches(f, 20, stream, torch)
+            out[f"{label}_{name}"] = {
+                "elements_per_s": n_ * 20 / (region * 1e-3), "ms": statistics.mean(per),
+                "logical_gbps": 2 * n_ * ELEM / (statistics.mean(per) * 1e-3) / 1e9}
+        bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
+        del x, y
 
     # the paper's throughput bound: a random gather of the same size (no cipher, no scan)
     host = workloads.uniform_u64(N_MAIN, 2)
@@ -407,6 +468,7 @@ def profile_case(args):
     from paper_2106_06161_gb300 import build as bsbuild
     bsbuild.build()
     import paper_2106_06161_gb300 as bs
+    bs.bshuffle_set_strategy(STRATEGIES[args.strategy])
     n = args.profile_n
     x = torch.from_numpy(workloads.uniform_u64(n, SEED).view(np.int64)).cuda()
     y = torch.empty_like(x)

@@ -11,11 +11,13 @@
  * Proposition 1 (Sec. 4) shows that deleting the images >= n from a uniform
  * permutation of [0, 2^k) leaves a uniform permutation of [0, n).
  *
- * Every step runs on the GPU in one fused kernel per call: the bijection in
- * registers, the compaction as an in-tile scan chained across tiles by
- * decoupled look-back (single pass, Sec. 4 last paragraph and the
- * "Bijective2" variant of Sec. 6), the gather of each kept element once, and a
- * coalesced store into its compacted slot.
+ * Every step runs on the GPU.  The paper's design is one fused kernel per
+ * call: the bijection in registers, the compaction as an in-tile scan chained
+ * across tiles by decoupled look-back (single pass, Sec. 4 last paragraph and
+ * the "Bijective2" variant of Sec. 6), the gather of each kept element once,
+ * and a coalesced store into its compacted slot.  For inputs much larger than
+ * L2 and of power-of-two length, bshuffle_permute can instead run a staged
+ * variant with the same output (see bshuffle_set_strategy).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -191,6 +193,44 @@ int bshuffle_round_keys(uint64_t seed, uint32_t rounds, uint32_t *keys);
  * The caller must ensure no call of this library is still running.
  */
 int bshuffle_release_workspaces(void);
+
+/*
+ * How bshuffle_permute moves data (the output is identical either way):
+ *   BSHUFFLE_STRATEGY_SINGLE_PASS  one fused launch: bijection, scan with
+ *       decoupled look-back, one random read and one coalesced write per
+ *       element (the paper's "Bijective2", Sec. 6).  No extra memory beyond
+ *       the small workspace.
+ *   BSHUFFLE_STRATEGY_STAGED  for n = 2^k >= 4096 and 4, 8 or 16-byte
+ *       elements (other calls run the single pass): nothing is dropped, so
+ *       element b belongs in slot f^-1(b) (the inverse cipher of Sec. 3.2).
+ *       Pass 1 reads the input sequentially, inverts the cipher and buckets
+ *       (value, slot) by 8 MiB output window; pass 2 scatters each window
+ *       while it is resident in L2.  Random HBM accesses are rate-limited on
+ *       GB300, streaming ones are not.  Workspace n * (4 + elem_bytes) bytes
+ *       plus a little, allocated on first use per stream.
+ *   BSHUFFLE_STRATEGY_AUTO (default)  staged when it applies and
+ *       n * elem_bytes >= 256 MiB, else single pass; if the staged workspace
+ *       cannot be allocated the single pass runs instead.
+ * The setting is process-wide.  Returns BSHUFFLE_ERR_INVALID for other values.
+ */
+#define BSHUFFLE_STRATEGY_AUTO 0
+#define BSHUFFLE_STRATEGY_SINGLE_PASS 1
+#define BSHUFFLE_STRATEGY_STAGED 2
+int bshuffle_set_strategy(int strategy);
+int bshuffle_get_strategy(void);
+
+/*
+ * Per-pass timing (tracing aid, off by default).  While on, bshuffle_permute
+ * records CUDA events around each of its kernels on the caller's stream.
+ * bshuffle_last_pass_ms synchronises `stream` and writes the durations of the
+ * last bshuffle_permute call on it, in ms, to ms[0 .. capacity): one value for
+ * the single pass, two for the staged path (inverse cipher + destination
+ * buckets, window scatter).  Returns
+ * the number of passes recorded (0 if none) or a negative error.  Do not turn
+ * it on while capturing a stream.
+ */
+int bshuffle_set_pass_timing(int on);
+int bshuffle_last_pass_ms(void *stream, float *ms, int capacity);
 
 /*
  * Time limit of one look-back wait in nanoseconds (default 2e9).  When a

@@ -35,6 +35,13 @@ from ._lib import (
     bshuffle_release_workspaces,
     bshuffle_round_keys,
     bshuffle_set_lookback_timeout_ns,
+    bshuffle_set_strategy,
+    bshuffle_get_strategy,
+    bshuffle_set_pass_timing,
+    bshuffle_last_pass_ms,
+    BSHUFFLE_STRATEGY_AUTO,
+    BSHUFFLE_STRATEGY_SINGLE_PASS,
+    BSHUFFLE_STRATEGY_STAGED,
     bshuffle_version,
     error_string,
     load,
@@ -45,7 +52,9 @@ __all__ = [
     "batched", "batched_packed", "packed_descs", "get_error", "domain_bits", "round_keys", "row_bytes",
     "bshuffle_permute", "bshuffle_indices", "bshuffle_inverse", "bshuffle_batched",
     "bshuffle_get_error", "bshuffle_domain_bits", "bshuffle_round_keys",
-    "bshuffle_release_workspaces", "bshuffle_set_lookback_timeout_ns",
+    "bshuffle_release_workspaces", "bshuffle_set_lookback_timeout_ns", "bshuffle_set_strategy",
+    "bshuffle_get_strategy", "bshuffle_set_pass_timing", "bshuffle_last_pass_ms", "BSHUFFLE_STRATEGY_AUTO", "BSHUFFLE_STRATEGY_SINGLE_PASS",
+    "BSHUFFLE_STRATEGY_STAGED",
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
     "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",
 ]

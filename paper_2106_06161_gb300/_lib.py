@@ -25,6 +25,9 @@ BSHUFFLE_ERR_CUDA = -7
 BSHUFFLE_ERR_LOOKBACK_TIMEOUT = -8
 BSHUFFLE_ERR_DEVICE_BOUNDS = -9
 BSHUFFLE_ERR_INVALID = -10
+BSHUFFLE_STRATEGY_AUTO = 0
+BSHUFFLE_STRATEGY_SINGLE_PASS = 1
+BSHUFFLE_STRATEGY_STAGED = 2
 DEFAULT_ROUNDS = 24
 MAX_ROUNDS = 64
 MAX_N = 2**32 - 1
@@ -48,6 +51,10 @@ SIGNATURES = {
     "bshuffle_permute_static": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
     "bshuffle_mc_group_diff": (_int, [_p, _u64, _u64, _u64, _u32, _u32, _p, _p]),
     "bshuffle_random_gather": (_int, [_p, _p, _u64, _u32, _p]),
+    "bshuffle_set_strategy": (_int, [_int]),
+    "bshuffle_get_strategy": (_int, []),
+    "bshuffle_set_pass_timing": (_int, [_int]),
+    "bshuffle_last_pass_ms": (_int, [_p, _p, _int]),
 }
 
 _lock = threading.Lock()
@@ -152,6 +159,24 @@ def bshuffle_set_lookback_timeout_ns(ns: int) -> None:
 
 def bshuffle_debug_skip_publish(tile: int) -> None:
     _check(load().bshuffle_debug_skip_publish(tile), "bshuffle_debug_skip_publish")
+
+
+def bshuffle_set_strategy(strategy: int) -> None:
+    _check(load().bshuffle_set_strategy(strategy), "bshuffle_set_strategy")
+
+
+def bshuffle_get_strategy() -> int:
+    return load().bshuffle_get_strategy()
+
+
+def bshuffle_set_pass_timing(on: bool) -> None:
+    _check(load().bshuffle_set_pass_timing(1 if on else 0), "bshuffle_set_pass_timing")
+
+
+def bshuffle_last_pass_ms(stream: int = 0) -> list[float]:
+    buf = (ctypes.c_float * 8)()
+    count = _check(load().bshuffle_last_pass_ms(stream, ctypes.addressof(buf), 8), "bshuffle_last_pass_ms")
+    return [float(buf[i]) for i in range(count)]
 
 
 def bshuffle_version() -> int:

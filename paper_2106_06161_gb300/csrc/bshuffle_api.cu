@@ -27,6 +27,12 @@ constexpr uint64_t kMinStatusWords = 4096;
 
 std::atomic<uint64_t> g_timeout_ns{2000000000ull};
 std::atomic<int64_t> g_skip_publish{-1};
+std::atomic<int> g_strategy{BSHUFFLE_STRATEGY_AUTO};
+std::atomic<int> g_pass_timing{0};
+// Auto strategy: the staged path from this many input bytes on.
+constexpr uint64_t kStagedMinBytes = uint64_t{1} << 28;
+// Input/output window of one staged bucket.
+constexpr uint64_t kStagedWindowBytes = uint64_t{1} << 23;
 
 // ------------------------------------------------------------------ host math
 
@@ -74,6 +80,10 @@ struct Workspace {
     uint64_t status_words = 0;
     void *aux = nullptr;       // batched plan tables
     size_t aux_bytes = 0;
+    void *staged = nullptr;    // staged-path buffers
+    size_t staged_bytes = 0;
+    cudaEvent_t marks[3] = {};  // per-pass timing of the last permute (when enabled)
+    int marks_recorded = 0;     // 0: none, 2: single pass, 3: staged
     WsHeader *header() const { return static_cast<WsHeader *>(base); }
     uint64_t *status() const
     {
@@ -179,6 +189,21 @@ int check_common(uint64_t n, uint32_t rounds)
     return BSHUFFLE_OK;
 }
 
+// The workspace's timing events when per-pass timing is on (else null).
+cudaEvent_t *timing_marks(Workspace *ws)
+{
+    if (g_pass_timing.load() == 0) return nullptr;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (ws->marks[0] == nullptr) {
+        for (cudaEvent_t &ev : ws->marks)
+            if (cudaEventCreate(&ev) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+    }
+    return ws->marks;
+}
+
 // One fused launch over the whole domain of n.
 int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed, uint32_t rounds,
               Mode mode, void *stream_ptr)
@@ -202,8 +227,105 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     if (rc != BSHUFFLE_OK) return rc;
     a.ws = ws->header();
     a.status = ws->status();
+    cudaEvent_t *marks = mode == Mode::Gather ? timing_marks(ws) : nullptr;
+    if (marks != nullptr && cudaEventRecord(marks[0], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
     const cudaError_t e = rows ? bsh::launch_rows(a, mode, stream) : bsh::launch_elem(a, mode, elem_bytes, stream);
-    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (marks != nullptr) {
+        if (cudaEventRecord(marks[1], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+        ws->marks_recorded = 2;
+    } else if (mode == Mode::Gather) {
+        ws->marks_recorded = 0;
+    }
+    return BSHUFFLE_OK;
+}
+
+uint32_t ceil_log2(uint64_t v)
+{
+    uint32_t k = 0;
+    while ((uint64_t{1} << k) < v) ++k;
+    return k;
+}
+
+// Grows the stream's staged buffers to `bytes`.  Returns BSHUFFLE_ERR_CUDA
+// (after clearing the CUDA error) if the allocation fails.
+int acquire_staged(cudaStream_t stream, Workspace *ws, size_t bytes)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (ws->staged != nullptr && ws->staged_bytes >= bytes) return BSHUFFLE_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cap != cudaStreamCaptureStatusNone) return BSHUFFLE_ERR_INVALID;
+    if (ws->staged != nullptr) {
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+        cudaFree(ws->staged);
+        ws->staged = nullptr;
+        ws->staged_bytes = 0;
+    }
+    const size_t granule = size_t{1} << 26;
+    const size_t want = (bytes + granule - 1) / granule * granule;
+    void *p = nullptr;
+    e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ws->staged = p;
+    ws->staged_bytes = want;
+    return BSHUFFLE_OK;
+}
+
+// The staged path (kernels_staged.cu) for n = 2^k: same output as the fused
+// single pass.  Returns BSHUFFLE_ERR_CUDA without launching anything if its
+// buffers cannot be allocated.
+int run_staged(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed, uint32_t rounds,
+               void *stream_ptr)
+{
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    bsh::StagedArgs a{};
+    a.in = in;
+    a.out = out;
+    a.g = geometry_of(n);
+    if (a.g.domain != n) return BSHUFFLE_ERR_INVALID;
+    a.rounds = rounds;
+    fill_keys(seed, rounds, a.keys);
+    const uint32_t lg = ceil_log2(n);
+    uint32_t shift = ceil_log2(kStagedWindowBytes / elem_bytes);
+    if (lg > 12 && lg - 12 > shift) shift = lg - 12;  // at most 4096 buckets
+    if (shift > lg) shift = lg;
+    a.dst_shift = shift;
+    a.num_dst = static_cast<uint32_t>((n + (uint64_t{1} << shift) - 1) >> shift);
+
+    auto up = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+    const size_t off_dval = 0;
+    const size_t off_dpos = up(off_dval + n * elem_bytes);
+    const size_t off_cursor = up(off_dpos + n * sizeof(uint32_t));
+    const size_t total = up(off_cursor + a.num_dst * sizeof(uint32_t));
+
+    Workspace *ws = nullptr;
+    int rc = acquire_workspace(stream, kMinStatusWords, &ws);
+    if (rc != BSHUFFLE_OK) return rc;
+    rc = acquire_staged(stream, ws, total);
+    if (rc != BSHUFFLE_OK) return rc;
+    char *base = static_cast<char *>(ws->staged);
+    a.dval = base + off_dval;
+    a.dpos = reinterpret_cast<uint32_t *>(base + off_dpos);
+    a.dst_cursor = reinterpret_cast<uint32_t *>(base + off_cursor);
+    a.ws = ws->header();
+    cudaError_t e = cudaMemsetAsync(a.dst_cursor, 0, a.num_dst * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaEvent_t *marks = timing_marks(ws);
+    e = bsh::launch_staged(a, elem_bytes, stream, marks);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ws->marks_recorded = marks != nullptr ? 3 : 0;
+    return BSHUFFLE_OK;
+}
+
+// The staged path needs n = 2^k (nothing dropped, so the inverse cipher gives
+// every element's slot) and 4, 8 or 16-byte elements.
+bool staged_eligible(uint64_t n, uint32_t elem_bytes)
+{
+    return (elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 16) && n >= 2 * bsh::staged_tile_size() &&
+           (n & (n - 1)) == 0;
 }
 
 }  // namespace
@@ -239,6 +361,13 @@ int bshuffle_permute(const void *in, void *out, uint64_t n, uint32_t elem_bytes,
     if (n == 0) return BSHUFFLE_OK;
     rc = check_buffers(in, out, n, elem_bytes);
     if (rc != BSHUFFLE_OK) return rc;
+    const int strategy = g_strategy.load();
+    if (strategy != BSHUFFLE_STRATEGY_SINGLE_PASS && staged_eligible(n, elem_bytes) &&
+        (strategy == BSHUFFLE_STRATEGY_STAGED || n * elem_bytes >= kStagedMinBytes)) {
+        rc = run_staged(in, out, n, elem_bytes, seed, rounds, stream);
+        if (rc == BSHUFFLE_OK || strategy == BSHUFFLE_STRATEGY_STAGED) return rc;
+        // auto: the staged buffers could not be had; the single pass needs none
+    }
     return run_fused(in, out, n, elem_bytes, seed, rounds, Mode::Gather, stream);
 }
 
@@ -414,10 +543,50 @@ int bshuffle_release_workspaces(void)
         if (cudaSetDevice(kv.first.first) != cudaSuccess) rc = BSHUFFLE_ERR_CUDA;
         if (kv.second.base != nullptr && cudaFree(kv.second.base) != cudaSuccess) rc = BSHUFFLE_ERR_CUDA;
         if (kv.second.aux != nullptr && cudaFree(kv.second.aux) != cudaSuccess) rc = BSHUFFLE_ERR_CUDA;
+        if (kv.second.staged != nullptr && cudaFree(kv.second.staged) != cudaSuccess) rc = BSHUFFLE_ERR_CUDA;
+        for (cudaEvent_t ev : kv.second.marks)
+            if (ev != nullptr) cudaEventDestroy(ev);
         cudaSetDevice(cur);
     }
     g_workspaces.clear();
     return rc;
+}
+
+int bshuffle_set_strategy(int strategy)
+{
+    if (strategy != BSHUFFLE_STRATEGY_AUTO && strategy != BSHUFFLE_STRATEGY_SINGLE_PASS &&
+        strategy != BSHUFFLE_STRATEGY_STAGED)
+        return BSHUFFLE_ERR_INVALID;
+    g_strategy.store(strategy);
+    return BSHUFFLE_OK;
+}
+
+int bshuffle_get_strategy(void) { return g_strategy.load(); }
+
+int bshuffle_set_pass_timing(int on)
+{
+    g_pass_timing.store(on != 0 ? 1 : 0);
+    return BSHUFFLE_OK;
+}
+
+int bshuffle_last_pass_ms(void *stream_ptr, float *ms, int capacity)
+{
+    if (ms == nullptr && capacity > 0) return BSHUFFLE_ERR_NULL;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lock(g_mutex);
+    auto it = g_workspaces.find({device, reinterpret_cast<uintptr_t>(stream)});
+    if (it == g_workspaces.end() || it->second.marks_recorded < 2) return 0;
+    const int passes = it->second.marks_recorded - 1;
+    for (int i = 0; i < passes && i < capacity; ++i) {
+        e = cudaEventElapsedTime(&ms[i], it->second.marks[i], it->second.marks[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return passes;
 }
 
 int bshuffle_set_lookback_timeout_ns(uint64_t ns)

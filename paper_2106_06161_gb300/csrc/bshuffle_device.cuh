@@ -59,6 +59,46 @@ __device__ __forceinline__ void cipher_items(uint32_t (&left)[ITEMS], uint32_t (
     for (int j = 0; j < ITEMS; ++j) right[j] &= rmask;
 }
 
+// Inverse of M0 modulo 2^64 (Newton's iteration; M0 is odd).
+constexpr uint64_t inverse_mod_2_64(uint64_t a)
+{
+    uint64_t x = a;  // correct to 3 bits: a * a = 1 mod 8 for odd a
+    for (int i = 0; i < 5; ++i) x *= 2 - a * x;
+    return x;
+}
+constexpr uint32_t kM0InvLo = static_cast<uint32_t>(inverse_mod_2_64(kM0));
+static_assert(static_cast<uint32_t>(kM0) * kM0InvLo == 1u, "M0 inverse");
+
+// One inverse round, following the inversion steps of Sec. 3.2: recover
+// (B_k(L), b) from the new right half (G^-1: the odd bit b sits at the bottom
+// for odd k), L = B_k^-1(B_k(L)) by multiplying with M0^-1 modulo 2^L, and
+// R = F_k(L) xor L' from the recomputed high product word.  The state must be
+// masked (left < 2^L, right < 2^R).
+template <bool ODD>
+__device__ __forceinline__ void cipher_inverse_round(uint32_t &left, uint32_t &right, uint32_t key,
+                                                     uint32_t L, uint32_t lmask)
+{
+    const uint32_t b = ODD ? (right & 1u) : 0u;
+    const uint32_t bl = ODD ? (right >> 1) : right;
+    const uint32_t old_left = (bl * kM0InvLo) & lmask;
+    const uint32_t hi = __umulhi(static_cast<uint32_t>(kM0), old_left) + static_cast<uint32_t>(kM0 >> 32) * old_left;
+    right = ((left ^ hi ^ key) & lmask) | (b << L);
+    left = old_left;
+}
+
+// ITEMS independent inverse evaluations, rounds in reverse key order.
+template <bool ODD, int ITEMS>
+__device__ __forceinline__ void cipher_inverse_items(uint32_t (&left)[ITEMS], uint32_t (&right)[ITEMS],
+                                                     const uint32_t *keys, uint32_t rounds, const Geometry &g)
+{
+    const uint32_t L = g.L, lmask = g.lmask;
+    for (uint32_t r = rounds; r-- > 0;) {
+        const uint32_t key = keys[r];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) cipher_inverse_round<ODD>(left[j], right[j], key, L, lmask);
+    }
+}
+
 // ------------------------------------------------------------------ memory helpers
 
 __device__ __forceinline__ uint64_t ld_relaxed_gpu(const uint64_t *p)

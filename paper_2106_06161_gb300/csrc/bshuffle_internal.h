@@ -105,6 +105,32 @@ uint64_t batch_ring_words();
 // Enqueue the planning kernel and the persistent kernel (elem_bytes 1..16).
 cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream);
 
+// ------------------------------------------------------------------ staged path
+
+// The staged shuffle of power-of-two lengths (n == 2^k): same output as the
+// fused single pass, two streaming passes (see kernels_staged.cu).
+struct StagedArgs {
+    const void *in;
+    void *out;
+    Geometry g;             // g.n == g.domain
+    uint32_t rounds;
+    uint32_t dst_shift;     // log2 of a destination bucket (output window) in elements
+    uint32_t num_dst;       // destination buckets, <= 4096
+    uint32_t pad0;
+    void *dval;             // n values, destination-bucket major
+    uint32_t *dpos;         // n slot offsets within their destination bucket
+    uint32_t *dst_cursor;   // num_dst, zero at launch
+    WsHeader *ws;           // error word
+    uint32_t keys[kMaxRounds];
+};
+
+uint32_t staged_tile_size();
+// Enqueue the two passes (elem_bytes 4, 8 or 16); the caller zeroes the
+// cursors first.  marks, when not null, are 3 events recorded before P1,
+// between the passes and after P2.
+cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, cudaStream_t stream,
+                          cudaEvent_t *marks = nullptr);
+
 // ------------------------------------------------------------------ Monte Carlo
 
 // Fused permutation statistic: T[b] = mean(y[:n1]) - mean(y[n1:]) of x

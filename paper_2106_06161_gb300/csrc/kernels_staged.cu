@@ -1,0 +1,220 @@
+// Staged shuffle of power-of-two lengths much larger than L2: the same
+// permutation as the fused single pass (Algorithm 1, Sec. 4), with every HBM
+// access sequential and the random accesses confined to L2-resident windows.
+//
+// On GB300 a random 8-byte access to a multi-GiB array is bound by the HBM
+// random-access rate (~47 G accesses/s), far below the streaming bandwidth, so
+// the single pass that the paper designs around (one random read and one
+// write per element) runs at ~10 % of HBM bandwidth.  When n = 2^k no domain
+// index is dropped, slot j holds X[f(j)], and equivalently element b goes to
+// slot f^-1(b): the inverse cipher of Sec. 3.2 turns the gather into a
+// scatter whose source side is sequential.  Two passes:
+//
+//   P1  per chunk of 2,048 consecutive elements b: a coalesced read of X[b],
+//       the inverse cipher j = f^-1(b), and a counting sort of (value, j) by
+//       destination bucket (j >> dst_shift, an 8 MiB output window) in shared
+//       memory; each bucket's run is appended with one global atomic per
+//       bucket per chunk.
+//   P2  per chunk of one destination bucket: out[j] = value, random within an
+//       L2-resident output window whose lines leave L2 complete.
+//
+// Runs are appended in a nondeterministic order, but every element is placed
+// by its exact slot, so the output is deterministic and identical to the
+// single pass.
+#include <cstdint>
+
+#include "bshuffle_device.cuh"
+#include "bshuffle_internal.h"
+
+namespace bsh {
+namespace {
+
+using dev::kFull;
+
+constexpr int kSBlock = 256;
+constexpr int kSItems = 8;
+constexpr int kSWarps = kSBlock / 32;
+constexpr uint32_t kSTile = kSBlock * kSItems;
+
+// Exclusive scan of cnt[0..m) into start[0..m) by the whole CTA (kSBlock threads).
+__device__ __forceinline__ void block_exclusive_scan(const uint32_t *cnt, uint32_t *start, uint32_t m,
+                                                     uint32_t *s_warp)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t per = (m + kSBlock - 1) / kSBlock;
+    const uint32_t b0 = tid * per;
+    const uint32_t b1 = b0 + per < m ? b0 + per : m;
+    uint32_t sum = 0;
+    for (uint32_t q = b0; q < b1; ++q) sum += cnt[q];
+    const uint32_t incl = dev::warp_inclusive_scan(sum);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < static_cast<uint32_t>(kSWarps) ? s_warp[lane] : 0u;
+        const uint32_t wi = dev::warp_inclusive_scan(w);
+        if (lane < static_cast<uint32_t>(kSWarps)) s_warp[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = s_warp[warp] + incl - sum;
+    for (uint32_t q = b0; q < b1; ++q) {
+        start[q] = run;
+        run += cnt[q];
+    }
+}
+
+// Streaming read of data used once (evict-first in L1 and L2).
+// ------------------------------------------------------------------ P1
+
+template <class T, bool ODD>
+__global__ void __launch_bounds__(kSBlock) staged_bucket_kernel(const __grid_constant__ StagedArgs a)
+{
+    extern __shared__ uint32_t s_dyn[];  // 3 * num_dst words
+    uint32_t *s_cnt = s_dyn;
+    uint32_t *s_start = s_dyn + a.num_dst;
+    uint32_t *s_gbase = s_start + a.num_dst;
+    __shared__ T s_val[kSTile];
+    __shared__ uint32_t s_pos[kSTile];
+    __shared__ uint16_t s_bucket[kSTile];
+    __shared__ uint32_t s_warp[kSWarps];
+
+    const uint32_t tid = threadIdx.x;
+    const Geometry &g = a.g;
+    const uint32_t first = blockIdx.x * kSTile;  // n = 2^k is a multiple of kSTile
+    const T *in = static_cast<const T *>(a.in);
+    for (uint32_t q = tid; q < a.num_dst; q += kSBlock) s_cnt[q] = 0u;
+
+    T val[kSItems];
+    uint32_t left[kSItems], right[kSItems];
+#pragma unroll
+    for (int j = 0; j < kSItems; ++j) {
+        const uint32_t b = first + static_cast<uint32_t>(j * kSBlock) + tid;
+        val[j] = __ldcs(in + b);
+        left[j] = b >> g.R;
+        right[j] = b & g.rmask;
+    }
+    dev::cipher_inverse_items<ODD, kSItems>(left, right, a.keys, a.rounds, g);
+    uint32_t bucket[kSItems], pos[kSItems], slot[kSItems];
+#pragma unroll
+    for (int j = 0; j < kSItems; ++j) {
+        const uint32_t dst = (left[j] << g.R) | right[j];  // f^-1(b): the element's output slot
+        bucket[j] = dst >> a.dst_shift;
+        pos[j] = dst & ((1u << a.dst_shift) - 1u);
+    }
+    __syncthreads();  // s_cnt zeroed
+#pragma unroll
+    for (int j = 0; j < kSItems; ++j) slot[j] = atomicAdd(&s_cnt[bucket[j]], 1u);
+    __syncthreads();
+    block_exclusive_scan(s_cnt, s_start, a.num_dst, s_warp);
+    for (uint32_t q = tid; q < a.num_dst; q += kSBlock) {
+        const uint32_t c = s_cnt[q];
+        s_gbase[q] = c != 0u ? atomicAdd(&a.dst_cursor[q], c) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSItems; ++j) {
+        const uint32_t p = s_start[bucket[j]] + slot[j];
+        s_val[p] = val[j];
+        s_pos[p] = pos[j];
+        s_bucket[p] = static_cast<uint16_t>(bucket[j]);
+    }
+    __syncthreads();
+    T *dval = static_cast<T *>(a.dval);
+    const uint64_t bsize = uint64_t{1} << a.dst_shift;
+    for (uint32_t p = tid; p < kSTile; p += kSBlock) {
+        const uint32_t q = s_bucket[p];
+        const uint64_t off = static_cast<uint64_t>(s_gbase[q]) + (p - s_start[q]);
+        const uint64_t bucket_base = static_cast<uint64_t>(q) << a.dst_shift;
+        if (off < bsize) {
+            dval[bucket_base + off] = s_val[p];
+            a.dpos[bucket_base + off] = s_pos[p];
+        } else {
+            dev::record_error(a.ws, dev::kErrDeviceBounds, bucket_base + off);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ P2
+
+template <class T>
+__global__ void __launch_bounds__(kSBlock) staged_scatter_kernel(const __grid_constant__ StagedArgs a)
+{
+    const uint64_t n = a.g.n;
+    const uint64_t first = static_cast<uint64_t>(blockIdx.x) * kSTile;
+    const T *dval = static_cast<const T *>(a.dval);
+    T *out = static_cast<T *>(a.out);
+    T v[kSItems];
+    uint64_t dst[kSItems];
+#pragma unroll
+    for (int j = 0; j < kSItems; ++j) {
+        const uint64_t e = first + static_cast<uint64_t>(j * kSBlock) + threadIdx.x;
+        dst[j] = n;
+        if (e < n) {
+            v[j] = __ldcs(dval + e);
+            const uint64_t bucket_base = (e >> a.dst_shift) << a.dst_shift;
+            dst[j] = bucket_base + __ldcs(a.dpos + e);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kSItems; ++j) {
+        if (dst[j] < n) out[dst[j]] = v[j];
+        else if (first + static_cast<uint64_t>(j * kSBlock) + threadIdx.x < n)
+            dev::record_error(a.ws, dev::kErrDeviceBounds, dst[j]);
+    }
+}
+
+cudaError_t mark(cudaEvent_t *marks, int i, cudaStream_t stream)
+{
+    return marks != nullptr ? cudaEventRecord(marks[i], stream) : cudaSuccess;
+}
+
+template <class T>
+cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *marks)
+{
+    static bool configured[64] = {false};
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (!configured[device]) {
+        e = cudaFuncSetAttribute(staged_bucket_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 3 * 4096 * 4);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(staged_bucket_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     3 * 4096 * 4);
+        if (e != cudaSuccess) return e;
+        configured[device] = true;
+    }
+    const size_t dyn = 3u * a.num_dst * sizeof(uint32_t);
+    const unsigned chunks = static_cast<unsigned>(static_cast<uint64_t>(a.g.n) / kSTile);
+    e = mark(marks, 0, stream);
+    if (e != cudaSuccess) return e;
+    if (a.g.k & 1u)
+        staged_bucket_kernel<T, true><<<chunks, kSBlock, dyn, stream>>>(a);
+    else
+        staged_bucket_kernel<T, false><<<chunks, kSBlock, dyn, stream>>>(a);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = mark(marks, 1, stream);
+    if (e != cudaSuccess) return e;
+    staged_scatter_kernel<T><<<chunks, kSBlock, 0, stream>>>(a);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = mark(marks, 2, stream);
+    return e;
+}
+
+}  // namespace
+
+uint32_t staged_tile_size() { return kSTile; }
+
+cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, cudaStream_t stream, cudaEvent_t *marks)
+{
+    if (a.num_dst > 4096 || static_cast<uint64_t>(a.g.n) != a.g.domain || a.g.domain < 2 * kSTile)
+        return cudaErrorInvalidValue;
+    switch (elem_bytes) {
+    case 4: return launch_typed<unsigned int>(a, stream, marks);
+    case 8: return launch_typed<unsigned long long>(a, stream, marks);
+    case 16: return launch_typed<uint4>(a, stream, marks);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bsh

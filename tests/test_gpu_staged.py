@@ -1,0 +1,92 @@
+"""The staged strategy of bshuffle_permute (for n = 2^k: the inverse cipher
+turns the gather into a scatter with a sequential source side, then an
+L2-resident window scatter) must produce exactly the single pass's output:
+checked against the oracle across widths and sizes, against the single pass
+at larger sizes, and through the automatic choice at full size (the
+full-size tests in test_gpu_parity.py).  Lengths that are not powers of two
+must run the single pass under the staged setting."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from tests.gpu_helpers import assert_no_device_error, to_device, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_2106_06161_gb300 import build
+    build.build()
+    import paper_2106_06161_gb300
+    paper_2106_06161_gb300.load()
+    yield paper_2106_06161_gb300
+    paper_2106_06161_gb300.bshuffle_set_strategy(paper_2106_06161_gb300.BSHUFFLE_STRATEGY_AUTO)
+
+
+def _run(bs, x: np.ndarray, seed: int, strategy: int, rounds: int = 24) -> np.ndarray:
+    bs.bshuffle_set_strategy(strategy)
+    try:
+        y = bs.permute(to_device(x), seed, rounds)
+        assert_no_device_error()
+    finally:
+        bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
+    return to_host(y, x)
+
+
+@pytest.mark.parametrize("width", [4, 8, 16])
+def test_staged_matches_oracle(bs, width):
+    for n in (4096, 8192, 65536, 2**20, 2**22, 4097, 6000, 1_000_003):
+        for seed in (0, 5):
+            x = workloads.sweep_payload(n, width, seed)
+            got = _run(bs, x, seed, bs.BSHUFFLE_STRATEGY_STAGED)
+            assert np.array_equal(got, oracle.permute(x, seed)), (n, seed)
+
+
+@pytest.mark.parametrize("rounds", [0, 1, 24])
+def test_staged_rounds(bs, rounds):
+    x = workloads.uniform_u64(2**18, rounds)
+    assert np.array_equal(_run(bs, x, 3, bs.BSHUFFLE_STRATEGY_STAGED, rounds), oracle.permute(x, 3, rounds))
+
+
+def test_staged_equals_single_pass_large(bs):
+    for n, width in ((2**25, 8), (2**26, 4), (2**24, 16)):
+        x = workloads.sweep_payload(n, width, 9)
+        xd = to_device(x)
+        outs = []
+        for strategy in (bs.BSHUFFLE_STRATEGY_STAGED, bs.BSHUFFLE_STRATEGY_SINGLE_PASS):
+            bs.bshuffle_set_strategy(strategy)
+            outs.append(bs.permute(xd, 9))
+            assert_no_device_error()
+        bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
+        assert torch.equal(outs[0], outs[1]), (n, width)
+        js = np.random.default_rng(1).integers(0, n, 20_000)
+        idx = oracle.indices(n, 9)
+        got = outs[0][torch.from_numpy(js).cuda()].cpu().numpy()
+        assert np.array_equal(got.view(x.dtype).reshape(len(js), *x.shape[1:]), x[idx[js].astype(np.int64)])
+
+
+def test_staged_repeated_and_alternating(bs):
+    x = workloads.uniform_u32(2**21, 4)
+    want = oracle.permute(x, 12)
+    for _ in range(3):
+        assert np.array_equal(_run(bs, x, 12, bs.BSHUFFLE_STRATEGY_STAGED), want)
+        assert np.array_equal(_run(bs, x, 12, bs.BSHUFFLE_STRATEGY_SINGLE_PASS), want)
+
+
+def test_pass_timing_reports_each_kernel(bs):
+    x = torch.arange(2**22, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    bs.bshuffle_set_pass_timing(True)
+    try:
+        for strategy, passes in ((bs.BSHUFFLE_STRATEGY_STAGED, 2), (bs.BSHUFFLE_STRATEGY_SINGLE_PASS, 1)):
+            bs.bshuffle_set_strategy(strategy)
+            bs.permute(x, 1)
+            ms = bs.bshuffle_last_pass_ms(stream)
+            assert len(ms) == passes and all(t > 0 for t in ms)
+    finally:
+        bs.bshuffle_set_pass_timing(False)
+        bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
+    assert bs.bshuffle_get_strategy() == bs.BSHUFFLE_STRATEGY_AUTO
