@@ -27,20 +27,24 @@ constexpr int kErrDeviceBounds = -9;
 // The 64-bit product M0 * left supplies F (its high word, XORed with the
 // round key and the right half into the new left half, L' = F_k(L) xor R)
 // and the bijection B (its low word).  For odd k, G shifts B up one bit and
-// moves the top bit b of the old right half in underneath, so the new right
-// half carries L + 1 bits.  For even k the right half is left unmasked
-// between rounds: only its low L bits are read by the next round, and the
-// caller masks it once at the end.
+// moves the top bit b of the old right half (bit L) in underneath, so the new
+// right half carries L + 1 bits.
+// The right half is never masked between rounds: the next round reads only
+// its low L bits (masked into the new left half) and, for odd k, exactly its
+// bit L (the funnel shift below), so bits above its width are don't-care.
+// The caller masks it once after the last round.
 template <bool ODD>
 __device__ __forceinline__ void cipher_round(uint32_t &left, uint32_t &right, uint32_t key,
                                              uint32_t L, uint32_t lmask, uint32_t rmask)
 {
+    (void)rmask;
     const uint64_t prod = kM0 * static_cast<uint64_t>(left);
     const uint32_t hi = static_cast<uint32_t>(prod >> 32);
-    uint32_t lo = static_cast<uint32_t>(prod);
-    if (ODD) lo = (lo << 1) | (right >> L);
-    left = (hi ^ key ^ right) & lmask;
-    right = ODD ? (lo & rmask) : lo;
+    const uint32_t lo = static_cast<uint32_t>(prod);
+    const uint32_t new_left = (hi ^ key ^ right) & lmask;
+    // odd k: (lo << 1) | bit L of right
+    right = ODD ? __funnelshift_l(right << (31u - L), lo, 1u) : lo;
+    left = new_left;
 }
 
 // ITEMS independent evaluations, rounds outer so that the ITEMS dependency
@@ -70,19 +74,22 @@ constexpr uint32_t kM0InvLo = static_cast<uint32_t>(inverse_mod_2_64(kM0));
 static_assert(static_cast<uint32_t>(kM0) * kM0InvLo == 1u, "M0 inverse");
 
 // One inverse round, following the inversion steps of Sec. 3.2: recover
-// (B_k(L), b) from the new right half (G^-1: the odd bit b sits at the bottom
-// for odd k), L = B_k^-1(B_k(L)) by multiplying with M0^-1 modulo 2^L, and
-// R = F_k(L) xor L' from the recomputed high product word.  The state must be
-// masked (left < 2^L, right < 2^R).
+// (B_k(L), b) from the new right half (G^-1: for odd k the odd bit b sits at
+// the bottom and B_k(L) above it), L = B_k^-1(B_k(L)) by multiplying with
+// M0^-1 modulo 2^L, and R = F_k(L) xor L' from the recomputed high product
+// word.  The left half must be exact; the right half may carry don't-care
+// bits above its width (only its low L + 1 bits are read, and the product
+// with M0^-1 is masked to L bits), so it is masked once after the last round.
 template <bool ODD>
 __device__ __forceinline__ void cipher_inverse_round(uint32_t &left, uint32_t &right, uint32_t key,
                                                      uint32_t L, uint32_t lmask)
 {
-    const uint32_t b = ODD ? (right & 1u) : 0u;
     const uint32_t bl = ODD ? (right >> 1) : right;
     const uint32_t old_left = (bl * kM0InvLo) & lmask;
     const uint32_t hi = __umulhi(static_cast<uint32_t>(kM0), old_left) + static_cast<uint32_t>(kM0 >> 32) * old_left;
-    right = ((left ^ hi ^ key) & lmask) | (b << L);
+    const uint32_t x = left ^ hi ^ key;
+    // odd k: R in the low L bits and b (bit 0 of the old right half) at bit L
+    right = ODD ? ((x & lmask) | ((right << L) & ~lmask)) : x;
     left = old_left;
 }
 
@@ -97,6 +104,8 @@ __device__ __forceinline__ void cipher_inverse_items(uint32_t (&left)[ITEMS], ui
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) cipher_inverse_round<ODD>(left[j], right[j], key, L, lmask);
     }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) right[j] &= g.rmask;
 }
 
 // ------------------------------------------------------------------ memory helpers
