@@ -286,6 +286,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     bs.bshuffle_set_strategy(STRATEGIES[args.strategy])
+    # the library's autotuner picks the single-pass configuration per width
+    # (used for lengths that are not powers of two); a few seconds
+    from paper_2106_06161_gb300 import autotune
+    tuning = autotune.tune(widths=(ELEM,), n=2**26 + 1, reps=3, warmup=1, save=False)
 
     seed = SEED + rank
     host = workloads.uniform_u64(N_MAIN, seed)
@@ -326,35 +330,12 @@ def run_ours(args):
     passes = [statistics.mean(col) for col in zip(*pass_ms)]
     roofline, pass_lines = roofline_for(passes, bsbuild)
 
-    # e2e: pinned host in -> device -> shuffle -> host out, every step
-    e2e_steps = max(3, min(20, args.steps // 10))
-    hin = torch.from_numpy(host.view(np.int64)).pin_memory()
-    hout = torch.empty_like(hin).pin_memory()
-    for _ in range(2):
-        x.copy_(hin, non_blocking=True)
-        step()
-        hout.copy_(y, non_blocking=True)
-    torch.cuda.synchronize()
-    barrier(world)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        x.copy_(hin, non_blocking=True)
-        step()
-        hout.copy_(y, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-    e2e = {"value": N_MAIN * world * e2e_steps / (e2e_ms * 1e-3), "unit": "elements/s",
-           "h2d_bytes_per_step": N_MAIN * ELEM, "d2h_bytes_per_step": N_MAIN * ELEM,
-           "ms_per_step": e2e_ms / e2e_steps, "steps": e2e_steps}
+    e2e = e2e_pipeline(bs, torch, dev, host, seed, args, world)
     # the round trip is exact
     if rank == 0:
         idx = torch.randint(0, N_MAIN, (1 << 16,), device=dev)
         src = bs.indices(N_MAIN, seed)[idx]
         assert torch.equal(y[idx], x[src]), "shuffle output does not match its index sequence"
-    del hin, hout
 
     extra = {}
     if not args.no_extra and rank == 0:
@@ -384,6 +365,7 @@ def run_ours(args):
             "logical_gbps": 2 * N_MAIN * ELEM / (ms_per_step * 1e-3) / 1e9,
             "strategy": {0: "auto", 1: "single_pass", 2: "staged"}[bs.bshuffle_get_strategy()],
             "kernels_per_step": len(passes), "roofline": roofline, "passes": pass_lines,
+            "single_pass_tuning": tuning,
             "e2e": e2e, "gpu_launches": args.steps * len(passes), "clocks": clk,
             "cpu_baseline": cpu, "extra": extra,
         }
@@ -391,6 +373,64 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def e2e_pipeline(bs, torch, dev, host, seed, args, world):
+    """The same shuffle end to end from pinned host memory, through the C ABI.
+
+    Every step copies its input host->device, shuffles it and copies the
+    result device->host, all inside the timed region.  Steps are pipelined on
+    three streams with two device buffer pairs, so the copy-in of step i+1 and
+    the copy-out of step i-1 overlap the shuffle of step i.
+    """
+    steps = max(3, min(20, args.steps // 10))
+    hin = torch.from_numpy(host.view(np.int64)).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    xs = [torch.empty(N_MAIN, dtype=torch.int64, device=dev) for _ in range(2)]
+    ys = [torch.empty(N_MAIN, dtype=torch.int64, device=dev) for _ in range(2)]
+    s_in, s_run, s_out = (torch.cuda.Stream(dev) for _ in range(3))
+    ev = lambda: torch.cuda.Event(enable_timing=False)  # noqa: E731
+    copied_in = [ev(), ev()]
+    shuffled = [ev(), ev()]
+    copied_out = [ev(), ev()]
+
+    def run(count):
+        for i in range(count):
+            b = i % 2
+            if i >= 2:
+                s_in.wait_event(shuffled[b])       # x[b] is free once step i-2 has shuffled it
+            with torch.cuda.stream(s_in):
+                xs[b].copy_(hin, non_blocking=True)
+            copied_in[b].record(s_in)
+            s_run.wait_event(copied_in[b])
+            if i >= 2:
+                s_run.wait_event(copied_out[b])    # y[b] is free once step i-2 has been copied out
+            bs.bshuffle_permute(xs[b].data_ptr(), ys[b].data_ptr(), N_MAIN, ELEM, seed, ROUNDS, s_run.cuda_stream)
+            shuffled[b].record(s_run)
+            s_out.wait_event(shuffled[b])
+            with torch.cuda.stream(s_out):
+                hout.copy_(ys[b], non_blocking=True)
+            copied_out[b].record(s_out)
+
+    run(2)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s_in)
+    s_run.wait_event(e0)
+    s_out.wait_event(e0)
+    run(steps)
+    s_out.wait_stream(s_run)
+    s_out.wait_stream(s_in)
+    e1.record(s_out)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    del xs, ys, hin, hout
+    return {"value": N_MAIN * world * steps / (ms * 1e-3), "unit": "elements/s",
+            "h2d_bytes_per_step": N_MAIN * ELEM, "d2h_bytes_per_step": N_MAIN * ELEM,
+            "ms_per_step": ms / steps, "steps": steps,
+            "pipeline": "copy-in, shuffle and copy-out of consecutive steps overlap on three streams"}
 
 
 def secondary(bs, torch, dev, stream):

@@ -220,6 +220,24 @@ int bshuffle_set_strategy(int strategy);
 int bshuffle_get_strategy(void);
 
 /*
+ * Tuning of the single-pass kernel used by bshuffle_permute for 4, 8 and
+ * 16-byte elements.  Configuration c (0 <= c < bshuffle_tuning_configs())
+ * has `block` threads per CTA, `items` domain indices per thread (one tile is
+ * block * items indices) and `rounds_unrolled` rounds fixed at compile time
+ * (0: the round count is read at run time; a configuration with a fixed count
+ * serves only calls with that many rounds, others fall back to
+ * configuration 0).  Configuration 0 is the default.  The choice is
+ * process-wide per element width and changes speed only: every
+ * configuration computes the same output.  bshuffle_tuning_select returns
+ * BSHUFFLE_ERR_INVALID for other widths or indices; bshuffle_tuning_selected
+ * returns the current choice (0 for other widths).
+ */
+int bshuffle_tuning_configs(void);
+int bshuffle_tuning_describe(int config, int *block, int *items, int *rounds_unrolled);
+int bshuffle_tuning_select(uint32_t elem_bytes, int config);
+int bshuffle_tuning_selected(uint32_t elem_bytes);
+
+/*
  * Per-pass timing (tracing aid, off by default).  While on, bshuffle_permute
  * records CUDA events around each of its kernels on the caller's stream.
  * bshuffle_last_pass_ms synchronises `stream` and writes the durations of the

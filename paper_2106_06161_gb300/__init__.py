@@ -39,6 +39,9 @@ from ._lib import (
     bshuffle_get_strategy,
     bshuffle_set_pass_timing,
     bshuffle_last_pass_ms,
+    bshuffle_tuning_configs,
+    bshuffle_tuning_select,
+    bshuffle_tuning_selected,
     BSHUFFLE_STRATEGY_AUTO,
     BSHUFFLE_STRATEGY_SINGLE_PASS,
     BSHUFFLE_STRATEGY_STAGED,
@@ -53,7 +56,8 @@ __all__ = [
     "bshuffle_permute", "bshuffle_indices", "bshuffle_inverse", "bshuffle_batched",
     "bshuffle_get_error", "bshuffle_domain_bits", "bshuffle_round_keys",
     "bshuffle_release_workspaces", "bshuffle_set_lookback_timeout_ns", "bshuffle_set_strategy",
-    "bshuffle_get_strategy", "bshuffle_set_pass_timing", "bshuffle_last_pass_ms", "BSHUFFLE_STRATEGY_AUTO", "BSHUFFLE_STRATEGY_SINGLE_PASS",
+    "bshuffle_get_strategy", "bshuffle_set_pass_timing", "bshuffle_last_pass_ms",
+    "bshuffle_tuning_configs", "bshuffle_tuning_select", "bshuffle_tuning_selected", "BSHUFFLE_STRATEGY_AUTO", "BSHUFFLE_STRATEGY_SINGLE_PASS",
     "BSHUFFLE_STRATEGY_STAGED",
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
     "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",

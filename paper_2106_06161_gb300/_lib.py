@@ -55,6 +55,10 @@ SIGNATURES = {
     "bshuffle_get_strategy": (_int, []),
     "bshuffle_set_pass_timing": (_int, [_int]),
     "bshuffle_last_pass_ms": (_int, [_p, _p, _int]),
+    "bshuffle_tuning_configs": (_int, []),
+    "bshuffle_tuning_describe": (_int, [_int, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "bshuffle_tuning_select": (_int, [_u32, _int]),
+    "bshuffle_tuning_selected": (_int, [_u32]),
 }
 
 _lock = threading.Lock()
@@ -177,6 +181,25 @@ def bshuffle_last_pass_ms(stream: int = 0) -> list[float]:
     buf = (ctypes.c_float * 8)()
     count = _check(load().bshuffle_last_pass_ms(stream, ctypes.addressof(buf), 8), "bshuffle_last_pass_ms")
     return [float(buf[i]) for i in range(count)]
+
+
+def bshuffle_tuning_configs() -> list[dict]:
+    """Every configuration of the tunable single-pass kernel."""
+    out = []
+    for c in range(load().bshuffle_tuning_configs()):
+        b, i, r = _int(0), _int(0), _int(0)
+        _check(load().bshuffle_tuning_describe(c, ctypes.byref(b), ctypes.byref(i), ctypes.byref(r)),
+               "bshuffle_tuning_describe")
+        out.append({"config": c, "block": b.value, "items": i.value, "rounds_unrolled": r.value})
+    return out
+
+
+def bshuffle_tuning_select(elem_bytes: int, config: int) -> None:
+    _check(load().bshuffle_tuning_select(elem_bytes, config), "bshuffle_tuning_select")
+
+
+def bshuffle_tuning_selected(elem_bytes: int) -> int:
+    return load().bshuffle_tuning_selected(elem_bytes)
 
 
 def bshuffle_version() -> int:

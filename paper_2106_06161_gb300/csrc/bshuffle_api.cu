@@ -219,7 +219,8 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     a.timeout_ns = g_timeout_ns.load();
     fill_keys(seed, rounds, a.keys);
     const bool rows = (mode == Mode::Gather || mode == Mode::Scatter) && elem_bytes > 16;
-    const uint64_t tile = rows ? bsh::rows_tile_size() : bsh::elem_tile_size(elem_bytes, mode);
+    const int config = rows ? 0 : bsh::elem_config_for(elem_bytes, mode, rounds);
+    const uint64_t tile = rows ? bsh::rows_tile_size() : bsh::elem_tile_size(config);
     const uint64_t tiles = (a.g.domain + tile - 1) / tile;
     a.num_tiles = static_cast<uint32_t>(tiles);
     Workspace *ws = nullptr;
@@ -229,7 +230,8 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     a.status = ws->status();
     cudaEvent_t *marks = mode == Mode::Gather ? timing_marks(ws) : nullptr;
     if (marks != nullptr && cudaEventRecord(marks[0], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
-    const cudaError_t e = rows ? bsh::launch_rows(a, mode, stream) : bsh::launch_elem(a, mode, elem_bytes, stream);
+    const cudaError_t e =
+        rows ? bsh::launch_rows(a, mode, stream) : bsh::launch_elem(a, mode, elem_bytes, config, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     if (marks != nullptr) {
         if (cudaEventRecord(marks[1], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
@@ -563,6 +565,25 @@ int bshuffle_set_strategy(int strategy)
 
 int bshuffle_get_strategy(void) { return g_strategy.load(); }
 
+int bshuffle_tuning_configs(void) { return bsh::kNumElemConfigs; }
+
+int bshuffle_tuning_describe(int config, int *block, int *items, int *rounds_unrolled)
+{
+    if (config < 0 || config >= bsh::kNumElemConfigs) return BSHUFFLE_ERR_INVALID;
+    if (block == nullptr || items == nullptr || rounds_unrolled == nullptr) return BSHUFFLE_ERR_NULL;
+    *block = bsh::kElemConfigs[config].block;
+    *items = bsh::kElemConfigs[config].items;
+    *rounds_unrolled = bsh::kElemConfigs[config].rounds;
+    return BSHUFFLE_OK;
+}
+
+int bshuffle_tuning_select(uint32_t elem_bytes, int config)
+{
+    return bsh::select_elem_config(elem_bytes, config) == 0 ? BSHUFFLE_OK : BSHUFFLE_ERR_INVALID;
+}
+
+int bshuffle_tuning_selected(uint32_t elem_bytes) { return bsh::selected_elem_config(elem_bytes); }
+
 int bshuffle_set_pass_timing(int on)
 {
     g_pass_timing.store(on != 0 ? 1 : 0);
@@ -677,7 +698,7 @@ extern "C" int bshuffle_permute_static(const void *in, void *out, uint64_t n, ui
     a.skip_publish_tile = g_skip_publish.load();
     a.timeout_ns = g_timeout_ns.load();
     fill_keys(seed, rounds, a.keys);
-    const uint64_t tile = bsh::elem_tile_size(elem_bytes, Mode::Gather);
+    const uint64_t tile = bsh::elem_tile_size(0);
     const uint64_t tiles = (a.g.domain + tile - 1) / tile;
     if (tiles > kStaticTiles) return BSHUFFLE_ERR_TOO_LARGE;
     a.num_tiles = static_cast<uint32_t>(tiles);
@@ -691,6 +712,6 @@ extern "C" int bshuffle_permute_static(const void *in, void *out, uint64_t n, ui
     // status words carry the launch tag and need no clearing.
     cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    e = bsh::launch_elem(a, Mode::Gather, elem_bytes, stream);
+    e = bsh::launch_elem(a, Mode::Gather, elem_bytes, 0, stream);
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }

@@ -108,6 +108,22 @@ __device__ __forceinline__ void cipher_inverse_items(uint32_t (&left)[ITEMS], ui
     for (int j = 0; j < ITEMS; ++j) right[j] &= g.rmask;
 }
 
+// The same with the round count fixed at compile time (fully unrolled, so
+// each round key is a constant-bank operand).
+template <bool ODD, int ITEMS, int ROUNDS>
+__device__ __forceinline__ void cipher_items_fixed(uint32_t (&left)[ITEMS], uint32_t (&right)[ITEMS],
+                                                   const uint32_t *keys, const Geometry &g)
+{
+    const uint32_t L = g.L, lmask = g.lmask, rmask = g.rmask;
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) cipher_round<ODD>(left[j], right[j], keys[r], L, lmask, rmask);
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) right[j] &= rmask;
+}
+
 // ------------------------------------------------------------------ memory helpers
 
 __device__ __forceinline__ uint64_t ld_relaxed_gpu(const uint64_t *p)

@@ -59,13 +59,32 @@ enum class Mode : int {
     Index64 = 3,  // out[j] = (uint64) f(i_j)
 };
 
-// Domain indices per tile of the element kernels and of the row kernels.
-uint32_t elem_tile_size(uint32_t elem_bytes, Mode mode);
+// Configurations of the element kernel: CTA size, items per thread, and
+// rounds unrolled at compile time (0 = read at run time).  Configuration 0
+// is the default and is instantiated for every mode and width; the others
+// serve bshuffle_permute with 4, 8 or 16-byte elements.
+struct ElemConfig {
+    int block;
+    int items;
+    int rounds;
+};
+constexpr int kNumElemConfigs = 7;
+extern const ElemConfig kElemConfigs[kNumElemConfigs];
+
+// The configuration selected for a width (0 for untunable widths), the one a
+// call with this mode and round count uses, and selection (-1 if invalid).
+int selected_elem_config(uint32_t elem_bytes);
+int elem_config_for(uint32_t elem_bytes, Mode mode, uint32_t rounds);
+int select_elem_config(uint32_t elem_bytes, int config);
+
+// Domain indices per tile of an element-kernel configuration and of the
+// row kernels.
+uint32_t elem_tile_size(int config);
 uint32_t rows_tile_size();
 
-// Enqueue one fused launch of num_tiles CTAs.  elem_bytes selects the
-// element kernel (1, 2, 4, 8, 16) or the row kernel (multiple of 16, > 16).
-cudaError_t launch_elem(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream);
+// Enqueue one fused launch of num_tiles CTAs in configuration `config`.
+cudaError_t launch_elem(const TileArgs &a, Mode mode, uint32_t elem_bytes, int config, cudaStream_t stream);
+cudaError_t launch_gather_tuned(const TileArgs &a, uint32_t elem_bytes, int config, cudaStream_t stream);
 cudaError_t launch_rows(const TileArgs &a, Mode mode, cudaStream_t stream);
 
 // ------------------------------------------------------------------ batched

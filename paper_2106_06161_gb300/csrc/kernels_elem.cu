@@ -1,179 +1,78 @@
-// Fused single-pass kernels for elements of 1, 2, 4, 8 and 16 bytes
-// (Algorithm 1 of Sec. 4 fused as in the paper's "Bijective2", Sec. 6).
-//
-// One CTA owns one tile of BLOCK * ITEMS consecutive domain indices, taken
-// from a global ticket so that every predecessor of a tile is already
-// running (the look-back never waits on a CTA that has not started).
-// Thread t evaluates the indices base + j * BLOCK + t (j < ITEMS): for a fixed
-// j a warp covers 32 consecutive indices, so its kept elements land in
-// consecutive output slots and its stores coalesce without a shared-memory
-// staging step.
-//   1. bijection: ITEMS cipher evaluations per thread, in registers;
-//   2. gather:    the kept sources are loaded right away (Gather mode), so the
-//                 random reads are in flight during the scan and look-back;
-//   3. scan:      warp ballots + popc, one warp scans the per-(item, warp)
-//                 counts, publishes the tile aggregate and looks back;
-//   4. store:     out[prefix + rank] = value (Gather, Index) or
-//                 out[source] = in[prefix + rank] (Scatter).
+// Instantiations and dispatch of the fused single-pass element kernel
+// (elem_kernel.cuh) for every mode and width in its default configuration,
+// and the table of tuning configurations (the others are instantiated for
+// the permute path in kernels_elem_tuned.cu).
+#include <atomic>
 #include <cstdint>
 
-#include "bshuffle_device.cuh"
-#include "bshuffle_internal.h"
+#include "elem_kernel.cuh"
 
 namespace bsh {
+
+const ElemConfig kElemConfigs[kNumElemConfigs] = {
+    {256, 8, 0}, {256, 4, 0}, {256, 16, 0}, {512, 8, 0}, {128, 8, 0}, {256, 8, 24}, {512, 4, 0},
+};
+
 namespace {
 
-using dev::kFull;
-
-template <class T>
-__device__ __forceinline__ T load_nc(const T *p)
-{
-    return __ldg(p);
-}
-
-template <class T, Mode MODE, bool ODD, int BLOCK, int ITEMS>
-__global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant__ TileArgs a)
-{
-    constexpr int WARPS = BLOCK / 32;
-    constexpr int ENTRIES = ITEMS * WARPS;
-    __shared__ dev::TileShared<ENTRIES> st;
-
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        st.tile = atomicAdd(&a.ws->ticket, 1u);
-        st.tag = dev::ld_relaxed_gpu(&a.ws->tag);
-    }
-    __syncthreads();
-    const uint32_t tile = st.tile;
-    const uint32_t tag = st.tag;
-    if (tile >= a.num_tiles) {  // only a corrupted header could hand out such a ticket
-        if (threadIdx.x == 0) {
-            dev::record_error(a.ws, dev::kErrDeviceBounds, tile);
-            dev::finish_launch(a.ws, tag, gridDim.x);
-        }
-        return;
-    }
-    const uint32_t base = tile * static_cast<uint32_t>(BLOCK * ITEMS);
-
-    // 1. bijection
-    uint32_t left[ITEMS], right[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t i = base + static_cast<uint32_t>(j * BLOCK) + threadIdx.x;
-        left[j] = i >> a.g.R;
-        right[j] = i & a.g.rmask;
-    }
-    dev::cipher_items<ODD, ITEMS>(left, right, a.keys, a.rounds, a.g);
-
-    uint32_t src[ITEMS];
-    bool keep[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t i = base + static_cast<uint32_t>(j * BLOCK) + threadIdx.x;
-        src[j] = (left[j] << a.g.R) | right[j];
-        keep[j] = static_cast<uint64_t>(i) < a.g.domain && src[j] < a.g.n;
-    }
-
-    // 2. random reads issued before the scan
-    T val[ITEMS];
-    if constexpr (MODE == Mode::Gather) {
-        const T *in = static_cast<const T *>(a.in);
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j)
-            if (keep[j]) val[j] = load_nc(in + src[j]);
-    }
-
-    // 3. in-tile ranks and the tile's global prefix
-    uint32_t mask[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) mask[j] = __ballot_sync(kFull, keep[j]);
-    if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) st.counts[j * WARPS + warp] = __popc(mask[j]);
-    }
-    __syncthreads();
-    if (warp == 0)
-        dev::tile_scan_lookback<ENTRIES>(st, dev::StatusRing{a.status, ~0ull, 63u, tag}, tile, 0, a.timeout_ns,
-                                         a.skip_publish_tile, a.ws);
-    __syncthreads();
-    const uint32_t prefix = st.prefix;
-    const bool ok = st.ok != 0u;
-
-    // 4. compacted output
-    if (ok) {
-        const uint32_t lt = dev::lanemask_lt();
-        uint32_t dst[ITEMS];
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            dst[j] = prefix + st.counts[j * WARPS + warp] + __popc(mask[j] & lt);
-            if (keep[j] && dst[j] >= a.g.n) {
-                dev::record_error(a.ws, dev::kErrDeviceBounds, dst[j]);
-                keep[j] = false;
-            }
-        }
-        if constexpr (MODE == Mode::Gather) {
-            T *out = static_cast<T *>(a.out);
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (keep[j]) out[dst[j]] = val[j];
-        } else if constexpr (MODE == Mode::Index32 || MODE == Mode::Index64) {
-            T *out = static_cast<T *>(a.out);
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (keep[j]) out[dst[j]] = static_cast<T>(src[j]);
-        } else {  // Scatter: coalesced read of slot dst, random write to src
-            const T *in = static_cast<const T *>(a.in);
-            T *out = static_cast<T *>(a.out);
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (keep[j]) val[j] = load_nc(in + dst[j]);
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (keep[j]) out[src[j]] = val[j];
-        }
-    }
-    if (threadIdx.x == 0) dev::finish_launch(a.ws, tag, gridDim.x);
-}
-
-constexpr int kBlock = 256;
-constexpr int kItems = 8;
+std::atomic<int> g_selected[17] = {};  // per element width (index = bytes), 0 = default
 
 template <class T, Mode MODE>
-cudaError_t launch_typed(const TileArgs &a, cudaStream_t stream)
+cudaError_t launch_default(const TileArgs &a, cudaStream_t stream)
 {
-    const dim3 grid(a.num_tiles), block(kBlock);
-    if (a.g.k & 1u)
-        elem_tile_kernel<T, MODE, true, kBlock, kItems><<<grid, block, 0, stream>>>(a);
-    else
-        elem_tile_kernel<T, MODE, false, kBlock, kItems><<<grid, block, 0, stream>>>(a);
-    return cudaGetLastError();
+    return elem::launch_config<T, MODE, 256, 8, 0>(a, stream);
 }
 
 template <Mode MODE>
 cudaError_t launch_by_width(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream)
 {
     switch (elem_bytes) {
-    case 1: return launch_typed<unsigned char, MODE>(a, stream);
-    case 2: return launch_typed<unsigned short, MODE>(a, stream);
-    case 4: return launch_typed<unsigned int, MODE>(a, stream);
-    case 8: return launch_typed<unsigned long long, MODE>(a, stream);
-    case 16: return launch_typed<uint4, MODE>(a, stream);
+    case 1: return launch_default<unsigned char, MODE>(a, stream);
+    case 2: return launch_default<unsigned short, MODE>(a, stream);
+    case 4: return launch_default<unsigned int, MODE>(a, stream);
+    case 8: return launch_default<unsigned long long, MODE>(a, stream);
+    case 16: return launch_default<uint4, MODE>(a, stream);
     default: return cudaErrorInvalidValue;
     }
 }
 
+bool tunable_width(uint32_t elem_bytes) { return elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 16; }
+
 }  // namespace
 
-uint32_t elem_tile_size(uint32_t, Mode) { return static_cast<uint32_t>(kBlock * kItems); }
-
-cudaError_t launch_elem(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream)
+int select_elem_config(uint32_t elem_bytes, int config)
 {
+    if (!tunable_width(elem_bytes) || config < 0 || config >= kNumElemConfigs) return -1;
+    g_selected[elem_bytes].store(config);
+    return 0;
+}
+
+int selected_elem_config(uint32_t elem_bytes)
+{
+    return tunable_width(elem_bytes) ? g_selected[elem_bytes].load() : 0;
+}
+
+int elem_config_for(uint32_t elem_bytes, Mode mode, uint32_t rounds)
+{
+    if (mode != Mode::Gather || !tunable_width(elem_bytes)) return 0;
+    const int c = g_selected[elem_bytes].load();
+    const ElemConfig &cfg = kElemConfigs[c];
+    return (cfg.rounds == 0 || cfg.rounds == static_cast<int>(rounds)) ? c : 0;
+}
+
+uint32_t elem_tile_size(int config) { return static_cast<uint32_t>(kElemConfigs[config].block * kElemConfigs[config].items); }
+
+cudaError_t launch_elem(const TileArgs &a, Mode mode, uint32_t elem_bytes, int config, cudaStream_t stream)
+{
+    if (config != 0) {
+        if (mode != Mode::Gather) return cudaErrorInvalidValue;
+        return launch_gather_tuned(a, elem_bytes, config, stream);
+    }
     switch (mode) {
     case Mode::Gather: return launch_by_width<Mode::Gather>(a, elem_bytes, stream);
     case Mode::Scatter: return launch_by_width<Mode::Scatter>(a, elem_bytes, stream);
-    case Mode::Index32: return launch_typed<unsigned int, Mode::Index32>(a, stream);
-    case Mode::Index64: return launch_typed<unsigned long long, Mode::Index64>(a, stream);
+    case Mode::Index32: return launch_default<unsigned int, Mode::Index32>(a, stream);
+    case Mode::Index64: return launch_default<unsigned long long, Mode::Index64>(a, stream);
     }
     return cudaErrorInvalidValue;
 }
