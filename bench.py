@@ -470,6 +470,35 @@ def secondary(bs, torch, dev, stream):
         "logical_gbps": 2 * N_MAIN * ELEM / (statistics.mean(per) * 1e-3) / 1e9}
     del x, y
 
+    # rows: [65536 x 1024] FP32 and BF16 (4 KiB and 2 KiB rows), forward
+    # gather and backward scatter of the autograd row shuffle
+    for dtype, name in ((torch.float32, "fp32"), (torch.bfloat16, "bf16")):
+        rows = torch.randn(*workloads.ROWS_SHAPE, device=dev).to(dtype)
+        res = torch.empty_like(rows)
+        rb = rows.shape[1] * rows.element_size()
+        fwd = lambda: bs.bshuffle_permute(rows.data_ptr(), res.data_ptr(), rows.shape[0], rb, 7, ROUNDS, sptr)  # noqa: E731
+        bwd = lambda: bs.bshuffle_inverse(res.data_ptr(), rows.data_ptr(), rows.shape[0], rb, 7, ROUNDS, sptr)  # noqa: E731
+        for _ in range(3):
+            fwd()
+            bwd()
+        _, tf = timed_launches(fwd, 20, stream, torch)
+        _, tb = timed_launches(bwd, 20, stream, torch)
+        nbytes = 2 * rows.numel() * rows.element_size()
+        out[f"rows_65536x1024_{name}"] = {
+            "forward_ms": tf / 20, "backward_ms": tb / 20,
+            "forward_gbps": nbytes / (tf / 20 * 1e-3) / 1e9, "backward_gbps": nbytes / (tb / 20 * 1e-3) / 1e9}
+        del rows, res
+
+    # permutation Monte Carlo: 10,000 shuffles of 100,000 float32 + group-mean difference
+    xmc = torch.from_numpy(workloads.mc_samples()).to(dev)
+    T = torch.empty(workloads.MC_SHUFFLES, dtype=torch.float64, device=dev)
+    mc = lambda: bs.bshuffle_mc_group_diff(xmc.data_ptr(), xmc.numel(), workloads.MC_GROUP, 0,  # noqa: E731
+                                           workloads.MC_SHUFFLES, ROUNDS, T.data_ptr(), sptr)
+    for _ in range(2):
+        mc()
+    _, tmc = timed_launches(mc, 5, stream, torch)
+    out["mc_10000x100000_fp32"] = {"ms": tmc / 5, "shuffles_per_s": workloads.MC_SHUFFLES / (tmc / 5 * 1e-3)}
+
     # 4096 uneven instances, int32: one batched launch vs one plain launch each
     sizes = workloads.batched_sizes()
     data = torch.from_numpy(workloads.batched_payloads(sizes)).to(dev)

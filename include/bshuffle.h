@@ -141,6 +141,21 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
                      void *stream);
 
 /*
+ * The shuffle with the linear congruential bijection of Sec. 3.1 in place of
+ * VariablePhilox: Y[j] = X[f(i_j)] as in bshuffle_permute, with
+ * f(i) = (a i + c) mod 2^k, a odd (so f is a bijection of [0, 2^k)).  The
+ * paper gives no seed-to-(a, c) mapping; here a is the first SplitMix64
+ * output of `seed` with its low bit set and c the second, both reduced
+ * mod 2^k (bshuffle_lcg_params, a host helper).  Fast but statistically weak:
+ * at most 2^(2k-1) permutations, and Sec. 5 reports it failing the
+ * chi-squared test by orders of magnitude.  Single-pass kernel only;
+ * elem_bytes 1, 2, 4, 8 or 16.
+ */
+int bshuffle_permute_lcg(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                         void *stream);
+int bshuffle_lcg_params(uint64_t seed, uint64_t n, uint64_t *a, uint64_t *c);
+
+/*
  * Permutation Monte Carlo statistic fused with the shuffle (an application
  * named in Sec. 1; the shuffled data never leaves registers and nothing but T
  * is written).  For b in [0, count):

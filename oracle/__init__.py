@@ -69,6 +69,10 @@ def _load():
             "oracle_mc_statistics": (None, [p, u64, u64, u64, u64, u32, p]),
             "oracle_kendall_discordant": (u64, [p, p, u32]),
             "oracle_kendall_pairs": (None, [p, u32, u64, p]),
+            "oracle_lcg_params": (None, [u64, u32, p, p]),
+            "oracle_lcg": (u64, [u64, u32, u64, u64]),
+            "oracle_indices_lcg": (u64, [p, u64, u64]),
+            "oracle_sample_permutations_lcg": (None, [p, u32, u64, u64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -218,3 +222,39 @@ def kendall_pairs(perms: np.ndarray) -> np.ndarray:
     out = np.zeros(count // 2, dtype=np.uint64)
     _load().oracle_kendall_pairs(_ptr(perms), n, count // 2, _ptr(out))
     return out
+
+
+# ---------------------------------------------------------------- LCG (Sec. 3.1)
+
+def lcg_params(seed: int, k: int) -> tuple[int, int]:
+    """(a, c) of the LCG bijection for a seed on a 2^k domain (reading R6)."""
+    a = ctypes.c_uint64(0)
+    c = ctypes.c_uint64(0)
+    _load().oracle_lcg_params(seed & (2**64 - 1), k, ctypes.addressof(a), ctypes.addressof(c))
+    return a.value, c.value
+
+
+def lcg(x: int, k: int, a: int, c: int) -> int:
+    return int(_load().oracle_lcg(x, k, a, c))
+
+
+def indices_lcg(n: int, seed: int) -> np.ndarray:
+    """Algorithm 1 with the LCG of Sec. 3.1 as the bijection."""
+    idx = np.zeros(max(n, 1), dtype=np.uint64)
+    if n == 0:
+        return idx[:0]
+    got = _load().oracle_indices_lcg(_ptr(idx), n, seed & (2**64 - 1))
+    if got != n:
+        raise ValueError("LCG kept a wrong count")
+    return idx
+
+
+def permute_lcg(x: np.ndarray, seed: int) -> np.ndarray:
+    x = np.ascontiguousarray(x)
+    return x[indices_lcg(x.shape[0], seed).astype(np.int64)]
+
+
+def sample_permutations_lcg(n: int, count: int, seed0: int = 0) -> np.ndarray:
+    perms = np.zeros((count, n), dtype=np.uint32)
+    _load().oracle_sample_permutations_lcg(_ptr(perms), n, seed0, count)
+    return perms

@@ -318,6 +318,62 @@ void oracle_sample_permutations(uint32_t *perms, uint32_t n, uint64_t seed0, uin
 }
 
 /* ------------------------------------------------------------------ */
+/* LCG bijection (Sec. 3.1, Eq. lcg) on the same padded domain         */
+/* ------------------------------------------------------------------ */
+
+/*
+ * y = (a x + c) mod 2^k with a odd, so a is coprime to 2^k and x -> y is a
+ * bijection of [0, 2^k).  Reading R6: the paper gives no seed-to-(a, c)
+ * mapping; here a = (first SplitMix64 output of the seed) with its low bit
+ * set, c = the second output, both reduced mod 2^k.
+ */
+void oracle_lcg_params(uint64_t seed, uint32_t k, uint64_t *a, uint64_t *c)
+{
+    uint64_t state = seed;
+    uint64_t mask = oracle_mask(k);
+    *a = (oracle_splitmix64_next(&state) | 1) & mask;
+    *c = oracle_splitmix64_next(&state) & mask;
+}
+
+uint64_t oracle_lcg(uint64_t x, uint32_t k, uint64_t a, uint64_t c)
+{
+    return (a * x + c) & oracle_mask(k);
+}
+
+/* Algorithm 1 with the LCG as f: idx[j] = f(i_j). */
+uint64_t oracle_indices_lcg(uint64_t *idx, uint64_t n, uint64_t seed)
+{
+    uint32_t k = oracle_domain_bits(n);
+    uint64_t a, c, domain, i, j = 0;
+    if (n == 0 || k > 40)
+        return 0;
+    oracle_lcg_params(seed, k, &a, &c);
+    domain = (uint64_t)1 << k;
+    for (i = 0; i < domain; i++) {
+        uint64_t b = oracle_lcg(i, k, a, c);
+        if (b < n) {
+            if (j < n)
+                idx[j] = b;
+            j++;
+        }
+    }
+    return j;
+}
+
+/* count LCG permutations of length n from seeds seed0, seed0+1, ... */
+void oracle_sample_permutations_lcg(uint32_t *perms, uint32_t n, uint64_t seed0, uint64_t count)
+{
+    uint64_t s, j;
+    uint64_t *idx = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+    for (s = 0; s < count; s++) {
+        oracle_indices_lcg(idx, n, seed0 + s);
+        for (j = 0; j < n; j++)
+            perms[s * n + j] = (uint32_t)idx[j];
+    }
+    free(idx);
+}
+
+/* ------------------------------------------------------------------ */
 /* Fisher-Yates (Sec. 1): the sequential baseline, timing only          */
 /* ------------------------------------------------------------------ */
 

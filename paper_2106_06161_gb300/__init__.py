@@ -40,6 +40,8 @@ from ._lib import (
     bshuffle_set_pass_timing,
     bshuffle_last_pass_ms,
     bshuffle_tuning_configs,
+    bshuffle_permute_lcg,
+    bshuffle_lcg_params,
     bshuffle_tuning_select,
     bshuffle_tuning_selected,
     BSHUFFLE_STRATEGY_AUTO,
@@ -57,7 +59,8 @@ __all__ = [
     "bshuffle_get_error", "bshuffle_domain_bits", "bshuffle_round_keys",
     "bshuffle_release_workspaces", "bshuffle_set_lookback_timeout_ns", "bshuffle_set_strategy",
     "bshuffle_get_strategy", "bshuffle_set_pass_timing", "bshuffle_last_pass_ms",
-    "bshuffle_tuning_configs", "bshuffle_tuning_select", "bshuffle_tuning_selected", "BSHUFFLE_STRATEGY_AUTO", "BSHUFFLE_STRATEGY_SINGLE_PASS",
+    "bshuffle_tuning_configs", "bshuffle_tuning_select", "bshuffle_tuning_selected",
+    "bshuffle_permute_lcg", "bshuffle_lcg_params", "permute_lcg", "BSHUFFLE_STRATEGY_AUTO", "BSHUFFLE_STRATEGY_SINGLE_PASS",
     "BSHUFFLE_STRATEGY_STAGED",
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
     "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",
@@ -238,3 +241,12 @@ def mc_pvalue(x: torch.Tensor, n1: int, base_seed: int, count: int, rounds: int 
 
 
 from .autograd import BShuffleRows, shuffle_rows  # noqa: E402
+
+
+def permute_lcg(x: torch.Tensor, seed: int, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Shuffle x along dim 0 with the LCG bijection of Sec. 3.1 (fast, weak)."""
+    _require_cuda(x, "x")
+    x = x.contiguous()
+    out = _out_like(x, out)
+    bshuffle_permute_lcg(x.data_ptr(), out.data_ptr(), x.shape[0], row_bytes(x), seed, _stream_of(x))
+    return out

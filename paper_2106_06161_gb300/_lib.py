@@ -59,6 +59,8 @@ SIGNATURES = {
     "bshuffle_tuning_describe": (_int, [_int, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "bshuffle_tuning_select": (_int, [_u32, _int]),
     "bshuffle_tuning_selected": (_int, [_u32]),
+    "bshuffle_permute_lcg": (_int, [_p, _p, _u64, _u32, _u64, _p]),
+    "bshuffle_lcg_params": (_int, [_u64, _u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
 }
 
 _lock = threading.Lock()
@@ -200,6 +202,18 @@ def bshuffle_tuning_select(elem_bytes: int, config: int) -> None:
 
 def bshuffle_tuning_selected(elem_bytes: int) -> int:
     return load().bshuffle_tuning_selected(elem_bytes)
+
+
+def bshuffle_permute_lcg(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, seed: int, stream: int = 0) -> None:
+    _check(load().bshuffle_permute_lcg(in_ptr, out_ptr, n, elem_bytes, seed & (2**64 - 1), stream),
+           "bshuffle_permute_lcg")
+
+
+def bshuffle_lcg_params(seed: int, n: int) -> tuple[int, int]:
+    a, c = _u64(0), _u64(0)
+    _check(load().bshuffle_lcg_params(seed & (2**64 - 1), n, ctypes.byref(a), ctypes.byref(c)),
+           "bshuffle_lcg_params")
+    return a.value, c.value
 
 
 def bshuffle_version() -> int:

@@ -458,6 +458,52 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 
+int bshuffle_lcg_params(uint64_t seed, uint64_t n, uint64_t *a, uint64_t *c)
+{
+    if (a == nullptr || c == nullptr) return BSHUFFLE_ERR_NULL;
+    if (n > BSHUFFLE_MAX_N) return BSHUFFLE_ERR_TOO_LARGE;
+    const uint32_t k = domain_bits_of(n);
+    const uint64_t mask = k >= 64 ? ~uint64_t{0} : ((uint64_t{1} << k) - 1);
+    uint64_t state = seed;
+    *a = (splitmix64(state) | 1) & mask;
+    *c = splitmix64(state) & mask;
+    return BSHUFFLE_OK;
+}
+
+int bshuffle_permute_lcg(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                         void *stream_ptr)
+{
+    int rc = check_common(n, 0);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (elem_bytes != 1 && elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16)
+        return BSHUFFLE_ERR_ELEM;
+    if (n == 0) return BSHUFFLE_OK;
+    rc = check_buffers(in, out, n, elem_bytes);
+    if (rc != BSHUFFLE_OK) return rc;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    TileArgs a{};
+    a.in = in;
+    a.out = out;
+    a.g = geometry_of(n);
+    a.elem_bytes = elem_bytes;
+    a.skip_publish_tile = g_skip_publish.load();
+    a.timeout_ns = g_timeout_ns.load();
+    uint64_t la = 0, lc = 0;
+    bshuffle_lcg_params(seed, n, &la, &lc);
+    a.lcg_a = static_cast<uint32_t>(la);
+    a.lcg_c = static_cast<uint32_t>(lc);
+    const uint64_t tile = bsh::elem_tile_size(0);
+    const uint64_t tiles = (a.g.domain + tile - 1) / tile;
+    a.num_tiles = static_cast<uint32_t>(tiles);
+    Workspace *ws = nullptr;
+    rc = acquire_workspace(stream, tiles, &ws);
+    if (rc != BSHUFFLE_OK) return rc;
+    a.ws = ws->header();
+    a.status = ws->status();
+    const cudaError_t e = bsh::launch_gather_lcg(a, elem_bytes, stream);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
 int bshuffle_mc_group_diff(const float *x, uint64_t n, uint64_t n1, uint64_t base_seed, uint32_t count,
                            uint32_t rounds, double *T, void *stream)
 {

@@ -48,6 +48,7 @@ struct TileArgs {
     uint64_t timeout_ns;        // look-back wait limit
     WsHeader *ws;
     uint64_t *status;           // one word per tile
+    uint32_t lcg_a, lcg_c;      // LCG bijection (odd a), both reduced mod 2^k
     uint32_t keys[kMaxRounds];
 };
 
@@ -85,6 +86,8 @@ uint32_t rows_tile_size();
 // Enqueue one fused launch of num_tiles CTAs in configuration `config`.
 cudaError_t launch_elem(const TileArgs &a, Mode mode, uint32_t elem_bytes, int config, cudaStream_t stream);
 cudaError_t launch_gather_tuned(const TileArgs &a, uint32_t elem_bytes, int config, cudaStream_t stream);
+// The fused gather with the LCG bijection (default configuration).
+cudaError_t launch_gather_lcg(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream);
 cudaError_t launch_rows(const TileArgs &a, Mode mode, cudaStream_t stream);
 
 // ------------------------------------------------------------------ batched

@@ -17,7 +17,9 @@
 //   4. store:     out[prefix + rank] = value (Gather, Index) or
 //                 out[source] = in[prefix + rank] (Scatter).
 // ROUNDS = 0 reads the round count at run time; ROUNDS > 0 unrolls exactly
-// that many rounds (valid only for calls with rounds == ROUNDS).
+// that many rounds (valid only for calls with rounds == ROUNDS).  BIJ selects
+// the bijection: VariablePhilox (Sec. 3.2) or the LCG of Sec. 3.1,
+// b = (a i + c) mod 2^k with a odd.
 #pragma once
 
 #include <cstdint>
@@ -30,13 +32,15 @@ namespace elem {
 
 using dev::kFull;
 
+enum Bijection : int { kVarPhilox = 0, kLcg = 1 };
+
 template <class T>
 __device__ __forceinline__ T load_nc(const T *p)
 {
     return __ldg(p);
 }
 
-template <class T, Mode MODE, bool ODD, int BLOCK, int ITEMS, int ROUNDS>
+template <class T, Mode MODE, bool ODD, int BLOCK, int ITEMS, int ROUNDS, int BIJ = kVarPhilox>
 __global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant__ TileArgs a)
 {
     constexpr int WARPS = BLOCK / 32;
@@ -69,17 +73,24 @@ __global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant_
         left[j] = i >> a.g.R;
         right[j] = i & a.g.rmask;
     }
-    if constexpr (ROUNDS > 0)
-        dev::cipher_items_fixed<ODD, ITEMS, ROUNDS>(left, right, a.keys, a.g);
-    else
-        dev::cipher_items<ODD, ITEMS>(left, right, a.keys, a.rounds, a.g);
+    if constexpr (BIJ == kVarPhilox) {
+        if constexpr (ROUNDS > 0)
+            dev::cipher_items_fixed<ODD, ITEMS, ROUNDS>(left, right, a.keys, a.g);
+        else
+            dev::cipher_items<ODD, ITEMS>(left, right, a.keys, a.rounds, a.g);
+    }
 
     uint32_t src[ITEMS];
     bool keep[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t i = base + static_cast<uint32_t>(j * BLOCK) + threadIdx.x;
-        src[j] = (left[j] << a.g.R) | right[j];
+        if constexpr (BIJ == kLcg) {
+            const uint32_t dmask = a.g.k >= 32 ? 0xffffffffu : ((1u << a.g.k) - 1u);
+            src[j] = (a.lcg_a * i + a.lcg_c) & dmask;  // mod 2^k of the 32-bit wrap is mod 2^k
+        } else {
+            src[j] = (left[j] << a.g.R) | right[j];
+        }
         keep[j] = static_cast<uint64_t>(i) < a.g.domain && src[j] < a.g.n;
     }
 

@@ -136,9 +136,13 @@ __global__ void __launch_bounds__(kSBlock) staged_bucket_kernel(const __grid_con
 // ------------------------------------------------------------------ P2
 
 // P2: each thread moves kSItems entries (reads first, then the stores).
-// Measured on GB300: more independent random stores in flight per SM (e.g.
-// 16 per thread with paired vector loads) slows this pass down; the L2 takes
-// random 8-byte writes at a bounded rate.
+// Measured on GB300: more independent random stores in flight per SM (16 per
+// thread with paired vector loads, or more than 5 resident CTAs) slows this
+// pass down; the L2 takes random 8-byte writes at a bounded rate.  The launch
+// reserves shared memory to keep at most kScatterCtasPerSm CTAs per SM.
+constexpr int kScatterCtasPerSm = 5;
+constexpr size_t kScatterSmemReserve = (228u * 1024u) / kScatterCtasPerSm - 1024u;
+
 template <class T>
 __global__ void __launch_bounds__(kSBlock) staged_scatter_kernel(const __grid_constant__ StagedArgs a)
 {
@@ -180,6 +184,9 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(staged_bucket_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      3 * 4096 * 4);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(staged_scatter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(kScatterSmemReserve));
         if (e != cudaSuccess) return e;
         configured[device] = true;
     }
@@ -194,7 +201,7 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
     e = cudaGetLastError();
     if (e == cudaSuccess) e = mark(marks, 1, stream);
     if (e != cudaSuccess) return e;
-    staged_scatter_kernel<T><<<chunks, kSBlock, 0, stream>>>(a);
+    staged_scatter_kernel<T><<<chunks, kSBlock, kScatterSmemReserve, stream>>>(a);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = mark(marks, 2, stream);
     return e;

@@ -114,3 +114,10 @@ def test_binding_has_no_cpu_fallback():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "bshuffle_oracle" not in text, f
+
+
+def test_lcg_params_agree_with_oracle(lib):
+    from paper_2106_06161_gb300 import bshuffle_lcg_params
+    for seed in (0, 1, 77, 2**64 - 1):
+        for n in (5, 1000, 2**20 + 1, 2**28 + 12345):
+            assert bshuffle_lcg_params(seed, n) == oracle.lcg_params(seed, oracle.domain_bits(n))

@@ -232,3 +232,13 @@ def test_random_gather_measurement_kernel(width):
         bs.bshuffle_random_gather(xd.data_ptr(), out.data_ptr(), n, width, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         assert np.array_equal(to_host(out, x), x[_scramble(np.arange(n), k).astype(np.int64)])
+
+
+@pytest.mark.parametrize("width", [1, 4, 8, 16])
+def test_lcg_variant_matches_oracle(width):
+    for n in (1, 5, 17, 2049, 65537, 1_000_003):
+        x = _payload(n, width, 4)
+        y = bs.permute_lcg(to_device(x), 31)
+        assert_no_device_error()
+        want = x[oracle.indices_lcg(n, 31).astype(np.int64)]
+        assert np.array_equal(to_host(y, x), want), n

@@ -160,3 +160,18 @@ def test_literal_tiny_domains_are_affine():
         keys = oracle.round_keys(seed, 24)
         seen4.add(tuple(oracle.varphilox(np.arange(16, dtype=np.uint64), 4, keys).tolist()))
     assert len(seen4) > 250   # 4 bits: no longer affine, almost all distinct
+
+
+def test_lcg_is_a_bijection_with_constant_stride():
+    # Sec. 3.1: y = a x + c mod 2^k is a bijection when a is coprime to 2^k
+    # (odd); consecutive inputs map a constant stride a apart.
+    for k in range(4, 17):
+        for seed in (0, 9):
+            a, c = oracle.lcg_params(seed, k)
+            assert a % 2 == 1 and a < 2**k and c < 2**k
+            ys = [oracle.lcg(x, k, a, c) for x in range(2**k)] if k <= 10 else None
+            if ys is not None:
+                assert sorted(ys) == list(range(2**k))
+                assert all((ys[x + 1] - ys[x]) % 2**k == a for x in range(2**k - 1))
+    idx = oracle.indices_lcg(1000, 3)
+    assert np.array_equal(np.sort(idx), np.arange(1000, dtype=np.uint64))

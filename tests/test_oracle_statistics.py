@@ -100,3 +100,12 @@ def test_mmd_detects_too_few_rounds():
     idx = oracle.sample_permutations(100, 20_000, seed0=0, rounds=2)
     mmd = stats.mmd2_estimate(stats.ranks_from_indices(idx))
     assert abs(mmd) > stats.clt_threshold(100, 20_000), mmd
+
+
+def test_chi2_lcg_fails_in_the_paper_region():
+    # Sec. 5: the LCG bijective function gives a chi-squared statistic in the
+    # region of 500,000 at n = 5 (100,000 permutations).
+    perms = oracle.sample_permutations_lcg(5, 100_000, 0)
+    chi, _, crit = stats.chi2_uniform(stats.ranks_from_indices(perms))
+    assert 300_000 < chi < 800_000, chi
+    assert chi > 1000 * crit
