@@ -54,9 +54,11 @@ def _fingerprint(sources: list[str]) -> str:
 
 
 def kernel_fingerprint(source: str) -> str:
-    """Hash of one kernel translation unit, the headers it includes and the flags."""
+    """Hash of one kernel translation unit, every csrc header and the flags."""
     h = hashlib.sha256()
-    for name in (source, "bshuffle_device.cuh", "bshuffle_internal.h"):
+    headers = sorted(os.path.basename(f) for f in glob.glob(os.path.join(CSRC, "*.cuh")) +
+                     glob.glob(os.path.join(CSRC, "*.h")))
+    for name in [source] + headers:
         h.update(name.encode())
         with open(os.path.join(CSRC, name), "rb") as fh:
             h.update(fh.read())
