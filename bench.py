@@ -456,6 +456,24 @@ def secondary(bs, torch, dev, stream):
         bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
         del x, y
 
+    # the fusion experiment of Sec. 6 at worst-case padding: Bijective0
+    # (separate passes), Bijective1 (two-pass scan), Bijective2 (single pass)
+    for w in (20, 24, 28):
+        n_ = 2**w + 1
+        host = workloads.uniform_u64(n_, 3)
+        x = torch.from_numpy(host.view(np.int64)).to(dev)
+        y = torch.empty_like(x)
+        xp, yp = x.data_ptr(), y.data_ptr()
+        row = {}
+        for variant, name in ((0, "bijective0"), (1, "bijective1"), (2, "bijective2")):
+            f = lambda: bs.bshuffle_permute_ablation(xp, yp, n_, ELEM, 3, ROUNDS, variant, sptr)  # noqa: E731
+            for _ in range(3):
+                f()
+            per, region = timed_launches(f, 10, stream, torch)
+            row[name] = {"ms": region / 10, "m_items_per_s": n_ * 10 / (region * 1e-3) / 1e6}
+        out[f"fusion_ablation_2p{w}_plus_1_u64"] = row
+        del x, y
+
     # the paper's throughput bound: a random gather of the same size (no cipher, no scan)
     host = workloads.uniform_u64(N_MAIN, 2)
     x = torch.from_numpy(host.view(np.int64)).to(dev)

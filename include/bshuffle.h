@@ -156,6 +156,23 @@ int bshuffle_permute_lcg(const void *in, void *out, uint64_t n, uint32_t elem_by
 int bshuffle_lcg_params(uint64_t seed, uint64_t n, uint64_t *a, uint64_t *c);
 
 /*
+ * Measurement entry point for the fusion experiment of Sec. 6: the output of
+ * bshuffle_permute, computed with less kernel fusion.
+ *   variant 0  "Bijective0": three kernels - W[i] = f(i) for the whole
+ *              domain, stream compaction of W (entries below n, in order,
+ *              decoupled look-back), then the gather Y[j] = X[W'[j]].
+ *              Scratch 4 * 2^k + 4 * n bytes.
+ *   variant 1  "Bijective1": fused, with a two-pass scan: a reduce pass
+ *              evaluates f and counts per tile, the tile counts are scanned,
+ *              and a second pass evaluates f again, ranks and gathers.
+ *   variant 2  "Bijective2": the fused single pass (as bshuffle_permute
+ *              with BSHUFFLE_STRATEGY_SINGLE_PASS).
+ * Scratch lives in the stream's workspace.  elem_bytes 4, 8 or 16.
+ */
+int bshuffle_permute_ablation(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                              uint32_t rounds, int variant, void *stream);
+
+/*
  * Permutation Monte Carlo statistic fused with the shuffle (an application
  * named in Sec. 1; the shuffled data never leaves registers and nothing but T
  * is written).  For b in [0, count):

@@ -41,6 +41,7 @@ from ._lib import (
     bshuffle_last_pass_ms,
     bshuffle_tuning_configs,
     bshuffle_permute_lcg,
+    bshuffle_permute_ablation,
     bshuffle_lcg_params,
     bshuffle_tuning_select,
     bshuffle_tuning_selected,
@@ -60,7 +61,7 @@ __all__ = [
     "bshuffle_release_workspaces", "bshuffle_set_lookback_timeout_ns", "bshuffle_set_strategy",
     "bshuffle_get_strategy", "bshuffle_set_pass_timing", "bshuffle_last_pass_ms",
     "bshuffle_tuning_configs", "bshuffle_tuning_select", "bshuffle_tuning_selected",
-    "bshuffle_permute_lcg", "bshuffle_lcg_params", "permute_lcg", "BSHUFFLE_STRATEGY_AUTO", "BSHUFFLE_STRATEGY_SINGLE_PASS",
+    "bshuffle_permute_lcg", "bshuffle_lcg_params", "permute_lcg", "bshuffle_permute_ablation", "BSHUFFLE_STRATEGY_AUTO", "BSHUFFLE_STRATEGY_SINGLE_PASS",
     "BSHUFFLE_STRATEGY_STAGED",
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
     "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",

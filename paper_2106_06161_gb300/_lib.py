@@ -61,6 +61,7 @@ SIGNATURES = {
     "bshuffle_tuning_selected": (_int, [_u32]),
     "bshuffle_permute_lcg": (_int, [_p, _p, _u64, _u32, _u64, _p]),
     "bshuffle_lcg_params": (_int, [_u64, _u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "bshuffle_permute_ablation": (_int, [_p, _p, _u64, _u32, _u64, _u32, _int, _p]),
 }
 
 _lock = threading.Lock()
@@ -214,6 +215,12 @@ def bshuffle_lcg_params(seed: int, n: int) -> tuple[int, int]:
     _check(load().bshuffle_lcg_params(seed & (2**64 - 1), n, ctypes.byref(a), ctypes.byref(c)),
            "bshuffle_lcg_params")
     return a.value, c.value
+
+
+def bshuffle_permute_ablation(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, seed: int, rounds: int,
+                              variant: int, stream: int = 0) -> None:
+    _check(load().bshuffle_permute_ablation(in_ptr, out_ptr, n, elem_bytes, seed & (2**64 - 1), rounds, variant,
+                                            stream), "bshuffle_permute_ablation")
 
 
 def bshuffle_version() -> int:

@@ -70,6 +70,7 @@ Geometry geometry_of(uint64_t n)
     g.lmask = (1u << g.L) - 1u;
     g.rmask = g.R >= 32 ? 0xffffffffu : ((1u << g.R) - 1u);
     g.domain = uint64_t{1} << g.k;
+    g.odd_mul = 1u << (31u - g.L);
     return g;
 }
 
@@ -455,6 +456,51 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
     a.skip_publish_tile = g_skip_publish.load();
     a.ws = ws->header();
     const cudaError_t e = bsh::launch_batched(a, s);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
+int bshuffle_permute_ablation(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                              uint32_t rounds, int variant, void *stream_ptr)
+{
+    int rc = check_common(n, rounds);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16) return BSHUFFLE_ERR_ELEM;
+    if (variant < 0 || variant > 2) return BSHUFFLE_ERR_INVALID;
+    if (n == 0) return BSHUFFLE_OK;
+    rc = check_buffers(in, out, n, elem_bytes);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (variant == 2) return run_fused(in, out, n, elem_bytes, seed, rounds, Mode::Gather, stream_ptr);
+
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    bsh::AblationArgs a{};
+    a.in = in;
+    a.out = out;
+    a.g = geometry_of(n);
+    a.rounds = rounds;
+    a.timeout_ns = g_timeout_ns.load();
+    fill_keys(seed, rounds, a.keys);
+    const uint64_t tile = bsh::ablation_tile_size();
+    const uint64_t tiles = (a.g.domain + tile - 1) / tile;
+    a.num_tiles = static_cast<uint32_t>(tiles);
+    auto up = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
+    const size_t bytes = variant == 0 ? up(a.g.domain * sizeof(uint32_t)) + up(n * sizeof(uint32_t))
+                                      : 2 * up(tiles * sizeof(uint32_t));
+    Workspace *ws = nullptr;
+    rc = acquire_workspace(stream, tiles, &ws);
+    if (rc != BSHUFFLE_OK) return rc;
+    rc = acquire_staged(stream, ws, bytes);
+    if (rc != BSHUFFLE_OK) return rc;
+    char *base = static_cast<char *>(ws->staged);
+    if (variant == 0) {
+        a.w = reinterpret_cast<uint32_t *>(base);
+        a.j = reinterpret_cast<uint32_t *>(base + up(a.g.domain * sizeof(uint32_t)));
+    } else {
+        a.tile_count = reinterpret_cast<uint32_t *>(base);
+        a.tile_prefix = reinterpret_cast<uint32_t *>(base + up(tiles * sizeof(uint32_t)));
+    }
+    a.ws = ws->header();
+    a.status = ws->status();
+    const cudaError_t e = bsh::launch_ablation(a, elem_bytes, variant, stream);
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 

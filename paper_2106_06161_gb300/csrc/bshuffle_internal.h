@@ -27,12 +27,14 @@ struct WsHeader {
 // split into a left half of L = floor(k/2) bits and a right half of
 // R = ceil(k/2) bits (Sec. 3.2).
 struct Geometry {
-    uint32_t n;       // number of kept slots, n <= 2^32 - 1
-    uint32_t k;       // domain exponent, 4 <= k <= 32
-    uint32_t L, R;    // half widths
-    uint32_t lmask;   // 2^L - 1
-    uint32_t rmask;   // 2^R - 1
-    uint64_t domain;  // 2^k
+    uint32_t n;        // number of kept slots, n <= 2^32 - 1
+    uint32_t k;        // domain exponent, 4 <= k <= 32
+    uint32_t L, R;     // half widths
+    uint32_t lmask;    // 2^L - 1
+    uint32_t rmask;    // 2^R - 1
+    uint64_t domain;   // 2^k
+    uint32_t odd_mul;  // 2^(31 - L): multiplying by it moves bit L to bit 31
+    uint32_t pad0;
 };
 
 // Everything one fused tile launch needs, passed by value (param space).
@@ -152,6 +154,30 @@ uint32_t staged_tile_size();
 // between the passes and after P2.
 cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, cudaStream_t stream,
                           cudaEvent_t *marks = nullptr);
+
+// ------------------------------------------------------------------ fusion ablation
+
+// Algorithm 1 with less fusion (Sec. 6): Bijective0 (variant 0: transform,
+// compaction and gather as separate kernels) and Bijective1 (variant 1: fused
+// with a two-pass scan).  Same output as bshuffle_permute.
+struct AblationArgs {
+    const void *in;
+    void *out;
+    Geometry g;
+    uint32_t rounds;
+    uint32_t num_tiles;       // tiles of ablation_tile_size() domain indices
+    uint32_t *w;              // variant 0: the 2^k images
+    uint32_t *j;              // variant 0: the n kept images in order
+    uint32_t *tile_count;     // variant 1: kept per tile
+    uint32_t *tile_prefix;    // variant 1: exclusive scan of tile_count
+    uint64_t timeout_ns;
+    WsHeader *ws;
+    uint64_t *status;         // variant 0's compaction look-back
+    uint32_t keys[kMaxRounds];
+};
+
+uint32_t ablation_tile_size();
+cudaError_t launch_ablation(const AblationArgs &a, uint32_t elem_bytes, int variant, cudaStream_t stream);
 
 // ------------------------------------------------------------------ Monte Carlo
 

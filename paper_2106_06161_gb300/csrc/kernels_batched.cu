@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(kBBlock) batch_tile_kernel(const __grid_consta
                 s_job.g.lmask = (1u << (k / 2)) - 1u;
                 s_job.g.rmask = (k - k / 2) >= 32 ? 0xffffffffu : ((1u << (k - k / 2)) - 1u);
                 s_job.g.domain = uint64_t{1} << k;
+                s_job.g.odd_mul = 1u << (31u - k / 2);
             }
             const uint64_t seed = __shfl_sync(kFull, threadIdx.x == 0 ? a.descs[t].seed : 0ull, 0);
             for (uint32_t r = threadIdx.x; r < a.rounds; r += 32) s_keys[r] = splitmix_key(seed, r);

@@ -242,3 +242,18 @@ def test_lcg_variant_matches_oracle(width):
         assert_no_device_error()
         want = x[oracle.indices_lcg(n, 31).astype(np.int64)]
         assert np.array_equal(to_host(y, x), want), n
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_fusion_ablation_variants_match_oracle(variant):
+    # Sec. 6: Bijective0 (separate passes), Bijective1 (two-pass scan) and
+    # Bijective2 (single pass) compute the same shuffle.
+    stream = torch.cuda.current_stream().cuda_stream
+    for width in (4, 8, 16):
+        for n in (5, 2049, 65537, 1_000_003):
+            x = _payload(n, width, variant)
+            xd = to_device(x)
+            out = torch.empty_like(xd)
+            bs.bshuffle_permute_ablation(xd.data_ptr(), out.data_ptr(), n, width, 13, 24, variant, stream)
+            assert_no_device_error()
+            assert np.array_equal(to_host(out, x), oracle.permute(x, 13)), (width, n)
