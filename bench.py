@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     p.add_argument("--strategy", choices=["auto", "single_pass", "staged"], default="auto",
                    help="how bshuffle_permute moves data (identical output)")
+    p.add_argument("--profile-batched", type=int, default=0,
+                   help="only run warmup + steps batched launches over this many instances (for ncu)")
     p.add_argument("--profile-n", type=int, default=0,
                    help="only run warmup + steps launches of the uint64 shuffle at this n (for ncu)")
     return p.parse_args()
@@ -474,6 +476,19 @@ def secondary(bs, torch, dev, stream):
         out[f"fusion_ablation_2p{w}_plus_1_u64"] = row
         del x, y
 
+    # Sec. 5's round-count study on the GPU: MMD^2 of 100,000 shuffles per point
+    from paper_2106_06161_gb300 import stats as gst
+    study = {}
+    t0 = time.perf_counter()
+    for n_ in (5, 100, 1000):
+        for r_ in (4, 8, 12, 16, 20, 24):
+            res_ = gst.mmd_test(n_, 100_000, rounds=r_)
+            study[f"n{n_}_r{r_}"] = {"mmd2": res_["mmd2"], "clt": res_["clt_threshold"],
+                                     "passes_clt": res_["passes_clt"]}
+    torch.cuda.synchronize()
+    study["seconds"] = time.perf_counter() - t0
+    out["mmd_round_study_100000"] = study
+
     # the paper's throughput bound: a random gather of the same size (no cipher, no scan)
     host = workloads.uniform_u64(N_MAIN, 2)
     x = torch.from_numpy(host.view(np.int64)).to(dev)
@@ -569,9 +584,31 @@ def profile_case(args):
     print(json.dumps({"profile_n": n, "launch_ms": per, "elements_per_s": n * args.steps / (region * 1e-3)}))
 
 
+def profile_batched(args):
+    """warmup + steps batched launches over the first --profile-batched instances."""
+    import torch
+    from paper_2106_06161_gb300 import build as bsbuild
+    bsbuild.build()
+    import paper_2106_06161_gb300 as bs
+    sizes = workloads.batched_sizes()[:args.profile_batched]
+    data = torch.from_numpy(workloads.batched_payloads(sizes)).cuda()
+    res = torch.empty_like(data)
+    descs = bs.packed_descs(data, res, sizes, list(range(len(sizes))))
+    sptr = torch.cuda.current_stream().cuda_stream
+    f = lambda: bs.bshuffle_batched(descs.data_ptr(), len(sizes), 4, ROUNDS, sptr)  # noqa: E731
+    for _ in range(args.warmup):
+        f()
+    per, region = timed_launches(f, args.steps, torch.cuda.current_stream(), torch)
+    if bs.get_error() != 0:
+        raise SystemExit("device error")
+    print(json.dumps({"profile_batched": len(sizes), "elements": int(sizes.sum()), "launch_ms": per}))
+
+
 def main():
     args = parse()
-    if args.profile_n:
+    if args.profile_batched:
+        profile_batched(args)
+    elif args.profile_n:
         profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

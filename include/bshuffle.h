@@ -201,6 +201,20 @@ int bshuffle_mc_group_diff(const float *x, uint64_t n, uint64_t n1, uint64_t bas
 int bshuffle_random_gather(const void *in, void *out, uint64_t n, uint32_t elem_bytes, void *stream);
 
 /*
+ * GPU helpers for the statistical tests of Sec. 5 (not part of the shuffle).
+ * bshuffle_kendall_pairs: for each p < num_pairs, out[p] = n_dis(s, t) of the
+ * permutations s = perms[2p], t = perms[2p + 1] (rows of n uint32 ranks),
+ * n_dis = #{i < j : (s_i < s_j) != (t_i < t_j)}, the count in the Mallows
+ * kernel exp(-lambda n_dis / C(n, 2)); 1 <= n <= 4096.
+ * bshuffle_invert_rows: sigma[r][idx[r][j]] = j for each of `rows` rows of
+ * length n: the slot order of a shuffle (slot j holds element idx[j]) turned
+ * into each element's rank, the convention of Sec. 2.  Device pointers;
+ * asynchronous on `stream`.
+ */
+int bshuffle_kendall_pairs(const uint32_t *perms, uint32_t n, uint64_t num_pairs, uint64_t *out, void *stream);
+int bshuffle_invert_rows(const uint32_t *idx, uint32_t n, uint64_t rows, uint32_t *sigma, void *stream);
+
+/*
  * Synchronises `stream`, then returns and clears the first device-side error
  * recorded by calls on that stream since the last bshuffle_get_error:
  * BSHUFFLE_OK, BSHUFFLE_ERR_LOOKBACK_TIMEOUT or BSHUFFLE_ERR_DEVICE_BOUNDS (or

@@ -62,6 +62,8 @@ SIGNATURES = {
     "bshuffle_permute_lcg": (_int, [_p, _p, _u64, _u32, _u64, _p]),
     "bshuffle_lcg_params": (_int, [_u64, _u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "bshuffle_permute_ablation": (_int, [_p, _p, _u64, _u32, _u64, _u32, _int, _p]),
+    "bshuffle_kendall_pairs": (_int, [_p, _u32, _u64, _p, _p]),
+    "bshuffle_invert_rows": (_int, [_p, _u32, _u64, _p, _p]),
 }
 
 _lock = threading.Lock()
@@ -221,6 +223,14 @@ def bshuffle_permute_ablation(in_ptr: int, out_ptr: int, n: int, elem_bytes: int
                               variant: int, stream: int = 0) -> None:
     _check(load().bshuffle_permute_ablation(in_ptr, out_ptr, n, elem_bytes, seed & (2**64 - 1), rounds, variant,
                                             stream), "bshuffle_permute_ablation")
+
+
+def bshuffle_kendall_pairs(perms_ptr: int, n: int, num_pairs: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().bshuffle_kendall_pairs(perms_ptr, n, num_pairs, out_ptr, stream), "bshuffle_kendall_pairs")
+
+
+def bshuffle_invert_rows(idx_ptr: int, n: int, rows: int, sigma_ptr: int, stream: int = 0) -> None:
+    _check(load().bshuffle_invert_rows(idx_ptr, n, rows, sigma_ptr, stream), "bshuffle_invert_rows")
 
 
 def bshuffle_version() -> int:

@@ -585,6 +585,31 @@ int bshuffle_random_gather(const void *in, void *out, uint64_t n, uint32_t elem_
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 
+int bshuffle_kendall_pairs(const uint32_t *perms, uint32_t n, uint64_t num_pairs, uint64_t *out, void *stream)
+{
+    if (num_pairs == 0) return BSHUFFLE_OK;
+    if (perms == nullptr || out == nullptr) return BSHUFFLE_ERR_NULL;
+    if (n == 0 || n > bsh::kendall_max_n()) return BSHUFFLE_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(perms) % 4 != 0 || reinterpret_cast<uintptr_t>(out) % 8 != 0)
+        return BSHUFFLE_ERR_ALIGN;
+    const cudaError_t e = bsh::launch_kendall_pairs(perms, n, num_pairs, out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
+int bshuffle_invert_rows(const uint32_t *idx, uint32_t n, uint64_t rows, uint32_t *sigma, void *stream)
+{
+    if (rows == 0) return BSHUFFLE_OK;
+    if (idx == nullptr || sigma == nullptr) return BSHUFFLE_ERR_NULL;
+    if (n == 0) return BSHUFFLE_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(idx) % 4 != 0 || reinterpret_cast<uintptr_t>(sigma) % 4 != 0)
+        return BSHUFFLE_ERR_ALIGN;
+    const uint64_t a = reinterpret_cast<uintptr_t>(idx), b = reinterpret_cast<uintptr_t>(sigma);
+    const uint64_t bytes = rows * n * 4;
+    if (a < b + bytes && b < a + bytes) return BSHUFFLE_ERR_ALIAS;
+    const cudaError_t e = bsh::launch_invert_rows(idx, n, rows, sigma, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
 int bshuffle_get_error(void *stream_ptr)
 {
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);

@@ -179,6 +179,13 @@ struct AblationArgs {
 uint32_t ablation_tile_size();
 cudaError_t launch_ablation(const AblationArgs &a, uint32_t elem_bytes, int variant, cudaStream_t stream);
 
+// ------------------------------------------------------------------ statistics (Sec. 5)
+
+uint32_t kendall_max_n();
+cudaError_t launch_kendall_pairs(const uint32_t *perms, uint32_t n, uint64_t pairs, uint64_t *out,
+                                 cudaStream_t stream);
+cudaError_t launch_invert_rows(const uint32_t *idx, uint32_t n, uint64_t rows, uint32_t *sigma, cudaStream_t stream);
+
 // ------------------------------------------------------------------ Monte Carlo
 
 // Fused permutation statistic: T[b] = mean(y[:n1]) - mean(y[n1:]) of x
