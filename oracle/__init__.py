@@ -73,6 +73,7 @@ def _load():
             "oracle_lcg": (u64, [u64, u32, u64, u64]),
             "oracle_indices_lcg": (u64, [p, u64, u64]),
             "oracle_sample_permutations_lcg": (None, [p, u32, u64, u64]),
+            "oracle_shapley_voting": (None, [p, u64, u64, u64, u64, u32, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -222,6 +223,16 @@ def kendall_pairs(perms: np.ndarray) -> np.ndarray:
     out = np.zeros(count // 2, dtype=np.uint64)
     _load().oracle_kendall_pairs(_ptr(perms), n, count // 2, _ptr(out))
     return out
+
+
+def shapley_voting(weights: np.ndarray, quota: int, seed0: int, samples: int,
+                   rounds: int = DEFAULT_ROUNDS) -> np.ndarray:
+    """Pivot counts of the weighted voting game [quota; weights] over `samples`
+    player orders, order s being the shuffle with seed seed0 + s."""
+    w = np.ascontiguousarray(weights, dtype=np.uint32)
+    counts = np.zeros(max(w.size, 1), dtype=np.uint64)
+    _load().oracle_shapley_voting(_ptr(w), w.size, quota, seed0 & (2**64 - 1), samples, rounds, _ptr(counts))
+    return counts[:w.size]
 
 
 # ---------------------------------------------------------------- LCG (Sec. 3.1)

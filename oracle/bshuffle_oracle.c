@@ -497,3 +497,43 @@ void oracle_kendall_pairs(const uint32_t *perms, uint32_t n, uint64_t num_pairs,
     for (p = 0; p < num_pairs; p++)
         out[p] = oracle_kendall_discordant(perms + (2 * p) * n, perms + (2 * p + 1) * n, n);
 }
+
+/* ------------------------------------------------------------------ */
+/* Shapley values by permutation sampling (application named in Sec. 1) */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Weighted voting game v(S) = 1 if sum_{i in S} w_i >= quota, else 0.  The
+ * Shapley value of player i is the probability, over uniform orders of the
+ * players, that i is pivotal: the running weight of the players before i is
+ * below the quota and adding w_i reaches it.  Sample s orders the players by
+ * the shuffle of Algorithm 1 with seed seed0 + s (slot j holds player
+ * f(i_j)); counts[i] = number of samples in which player i is pivotal.
+ * With quota 0 or above the total weight no player is ever pivotal.
+ */
+void oracle_shapley_voting(const uint32_t *w, uint64_t n, uint64_t quota, uint64_t seed0,
+                           uint64_t samples, uint32_t rounds, uint64_t *counts)
+{
+    uint32_t keys[256];
+    uint32_t k;
+    uint64_t domain, s, i;
+    memset(counts, 0, sizeof(uint64_t) * n);
+    if (n == 0 || quota == 0 || rounds > 256)
+        return;
+    k = oracle_domain_bits(n);
+    domain = (uint64_t)1 << k;
+    for (s = 0; s < samples; s++) {
+        uint64_t before = 0;
+        oracle_round_keys(seed0 + s, rounds, keys);
+        for (i = 0; i < domain; i++) {
+            uint64_t player = oracle_varphilox(i, k, keys, rounds);
+            if (player >= n)
+                continue;
+            if (before < quota && before + w[player] >= quota) {
+                counts[player]++;
+                break;
+            }
+            before += w[player];
+        }
+    }
+}
