@@ -353,6 +353,16 @@ def run_ours(args):
                "kind": "oracle",
                "sample": f"first {slots} output slots of the same n=2^28 uint64 shuffle, 8 trials, "
                          f"single-threaded C oracle"}
+        # context: a sequential Fisher-Yates shuffle (the classical method of
+        # Sec. 1) of 2^22 uint64 keys, single thread
+        import oracle
+        fy = workloads.uniform_u64(2**22, 5)
+        fy_t = []
+        for t in range(3):
+            t0 = time.perf_counter()
+            oracle.fisher_yates(fy, t)
+            fy_t.append(time.perf_counter() - t0)
+        cpu["fisher_yates_2p22_u64_elements_per_s"] = 2**22 / min(fy_t)
 
     if rank == 0:
         line = {
@@ -531,6 +541,21 @@ def secondary(bs, torch, dev, stream):
         mc()
     _, tmc = timed_launches(mc, 5, stream, torch)
     out["mc_10000x100000_fp32"] = {"ms": tmc / 5, "shuffles_per_s": workloads.MC_SHUFFLES / (tmc / 5 * 1e-3)}
+
+    # Shapley values of a weighted voting game by permutation sampling:
+    # 10,000 players, simple majority, 100,000 sampled orders
+    wv = workloads.voting_weights()
+    wt = torch.from_numpy(wv.view(np.int32)).to(dev)
+    counts = torch.empty(wv.size, dtype=torch.int64, device=dev)
+    qv = workloads.majority_quota(wv)
+    sv = lambda: bs.bshuffle_shapley_voting(wt.data_ptr(), wv.size, qv, 0, workloads.VOTING_SAMPLES,  # noqa: E731
+                                            ROUNDS, counts.data_ptr(), sptr)
+    for _ in range(2):
+        sv()
+    _, tsv = timed_launches(sv, 5, stream, torch)
+    out["shapley_voting_10000_players_100000_orders"] = {
+        "ms": tsv / 5, "orders_per_s": workloads.VOTING_SAMPLES / (tsv / 5 * 1e-3),
+        "pivots": int(counts.sum().item())}
 
     # 4096 uneven instances, int32: one batched launch vs one plain launch each
     sizes = workloads.batched_sizes()

@@ -191,6 +191,25 @@ int bshuffle_mc_group_diff(const float *x, uint64_t n, uint64_t n1, uint64_t bas
                            uint32_t rounds, double *T, void *stream);
 
 /*
+ * Shapley values of a weighted voting game by permutation sampling (an
+ * application named in Sec. 1), fused with the shuffle; the player orders
+ * are never written.  Game [quota; w_0 .. w_{n-1}]: a coalition wins when
+ * its total weight reaches quota.  For s in [0, samples):
+ *     order = bshuffle_indices(n, seed = seed0 + s, rounds)
+ *     the player order[j] whose weight takes the running total of
+ *     order[0..j-1] from below quota to at least quota is pivotal:
+ *     counts[order[j]] += 1
+ *   weights  device array of n uint32 weights (caller-owned, read only)
+ *   counts   device array of n uint64 (caller-owned), overwritten
+ * counts / samples estimates each player's Shapley value.  With quota 0 or
+ * above the total weight no player is pivotal and counts stays zero.  The
+ * counts are exact integers: any order of the increments gives the same
+ * result.  Needs no workspace.  n = 0 is a no-op.
+ */
+int bshuffle_shapley_voting(const uint32_t *weights, uint64_t n, uint64_t quota, uint64_t seed0, uint64_t samples,
+                            uint32_t rounds, uint64_t *counts, void *stream);
+
+/*
  * Measurement kernel, not a shuffle API: out[i] = in[h(i)] for a fixed cheap
  * bijection h of [0, n) (three rounds of multiply-by-odd-constant and
  * xor-shift on k-bit values), with no cipher, keep test or scan.  It measures

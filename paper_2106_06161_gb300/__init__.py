@@ -31,6 +31,7 @@ from ._lib import (
     bshuffle_inverse,
     bshuffle_mc_group_diff,
     bshuffle_permute,
+    bshuffle_shapley_voting,
     bshuffle_random_gather,
     bshuffle_release_workspaces,
     bshuffle_round_keys,
@@ -65,6 +66,7 @@ __all__ = [
     "BSHUFFLE_STRATEGY_STAGED",
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
     "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",
+    "bshuffle_shapley_voting", "shapley_voting",
 ]
 
 
@@ -239,6 +241,24 @@ def mc_pvalue(x: torch.Tensor, n1: int, base_seed: int, count: int, rounds: int 
     t_obs = float(xd[:n1].mean() - xd[n1:].mean())
     exceed = int((T.abs() >= abs(t_obs)).sum())
     return (1 + exceed) / (count + 1), T, t_obs
+
+
+def shapley_voting(weights: torch.Tensor, quota: int, seed0: int, samples: int,
+                   rounds: int = DEFAULT_ROUNDS) -> torch.Tensor:
+    """Pivot counts of the weighted voting game [quota; weights] over `samples`
+    player orders (order s = the shuffle with seed seed0 + s), as int64.
+
+    counts / samples estimates the Shapley values.  `weights` is a 1-D CUDA
+    tensor of non-negative int32 (or uint32) weights.  One fused launch.
+    """
+    _require_cuda(weights, "weights")
+    if weights.dim() != 1 or weights.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise ValueError("weights must be a 1-D int32 or uint32 CUDA tensor")
+    weights = weights.contiguous()
+    counts = torch.empty(weights.numel(), dtype=torch.int64, device=weights.device)
+    bshuffle_shapley_voting(weights.data_ptr(), weights.numel(), quota, seed0, samples, rounds, counts.data_ptr(),
+                            _stream_of(weights))
+    return counts
 
 
 from .autograd import BShuffleRows, shuffle_rows  # noqa: E402

@@ -50,6 +50,7 @@ SIGNATURES = {
     "bshuffle_version": (_int, []),
     "bshuffle_permute_static": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
     "bshuffle_mc_group_diff": (_int, [_p, _u64, _u64, _u64, _u32, _u32, _p, _p]),
+    "bshuffle_shapley_voting": (_int, [_p, _u64, _u64, _u64, _u64, _u32, _p, _p]),
     "bshuffle_random_gather": (_int, [_p, _p, _u64, _u32, _p]),
     "bshuffle_set_strategy": (_int, [_int]),
     "bshuffle_get_strategy": (_int, []),
@@ -134,6 +135,12 @@ def bshuffle_mc_group_diff(x_ptr: int, n: int, n1: int, base_seed: int, count: i
                            t_ptr: int, stream: int = 0) -> None:
     _check(load().bshuffle_mc_group_diff(x_ptr, n, n1, base_seed & (2**64 - 1), count, rounds, t_ptr, stream),
            "bshuffle_mc_group_diff")
+
+
+def bshuffle_shapley_voting(w_ptr: int, n: int, quota: int, seed0: int, samples: int, rounds: int,
+                            counts_ptr: int, stream: int = 0) -> None:
+    _check(load().bshuffle_shapley_voting(w_ptr, n, quota, seed0 & (2**64 - 1), samples, rounds, counts_ptr, stream),
+           "bshuffle_shapley_voting")
 
 
 def bshuffle_random_gather(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, stream: int = 0) -> None:

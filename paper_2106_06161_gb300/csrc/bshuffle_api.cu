@@ -572,6 +572,31 @@ int bshuffle_mc_group_diff(const float *x, uint64_t n, uint64_t n1, uint64_t bas
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 
+int bshuffle_shapley_voting(const uint32_t *weights, uint64_t n, uint64_t quota, uint64_t seed0, uint64_t samples,
+                            uint32_t rounds, uint64_t *counts, void *stream)
+{
+    if (rounds > BSHUFFLE_MAX_ROUNDS) return BSHUFFLE_ERR_ROUNDS;
+    if (n > BSHUFFLE_MAX_N) return BSHUFFLE_ERR_TOO_LARGE;
+    if (n == 0) return BSHUFFLE_OK;
+    if (weights == nullptr || counts == nullptr) return BSHUFFLE_ERR_NULL;
+    if (reinterpret_cast<uintptr_t>(weights) % 4 != 0 || reinterpret_cast<uintptr_t>(counts) % 8 != 0)
+        return BSHUFFLE_ERR_ALIGN;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(counts, 0, n * sizeof(uint64_t), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (quota == 0 || samples == 0) return BSHUFFLE_OK;
+    bsh::ShapleyArgs a{};
+    a.w = weights;
+    a.counts = counts;
+    a.g = geometry_of(n);
+    a.quota = quota;
+    a.seed0 = seed0;
+    a.samples = samples;
+    a.rounds = rounds;
+    e = bsh::launch_shapley_voting(a, s);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
 int bshuffle_random_gather(const void *in, void *out, uint64_t n, uint32_t elem_bytes, void *stream)
 {
     if (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16) return BSHUFFLE_ERR_ELEM;

@@ -185,6 +185,28 @@ __device__ __forceinline__ uint32_t next_tag(uint32_t tag)
     return tag >= 0x7fffffffu ? 1u : tag + 1u;
 }
 
+// Round key r of a seed: the low 32 bits of the (r + 1)-th SplitMix64 output
+// started from the seed (Steele, Lea, Flood 2014), computed directly from r
+// so that every lane can derive its own key.
+__device__ __forceinline__ uint32_t splitmix_key(uint64_t seed, uint32_t r)
+{
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (static_cast<uint64_t>(r) + 1ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return static_cast<uint32_t>(z ^ (z >> 31));
+}
+
+__device__ __forceinline__ uint64_t warp_inclusive_scan64(uint64_t v)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t u = __shfl_up_sync(kFull, v, d);
+        if (lane >= static_cast<uint32_t>(d)) v += u;
+    }
+    return v;
+}
+
 __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v)
 {
     const uint32_t lane = threadIdx.x & 31u;

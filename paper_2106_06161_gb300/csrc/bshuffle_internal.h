@@ -203,6 +203,19 @@ struct McArgs {
 
 cudaError_t launch_mc(const McArgs &a, cudaStream_t stream);
 
+struct ShapleyArgs {
+    const uint32_t *w;  // player weights
+    uint64_t *counts;   // pivot counts per player, zeroed by the caller
+    Geometry g;         // g.n = number of players
+    uint64_t quota;
+    uint64_t seed0;
+    uint64_t samples;
+    uint32_t rounds;
+    uint32_t pad0;
+};
+
+cudaError_t launch_shapley_voting(const ShapleyArgs &a, cudaStream_t stream);
+
 // Measurement kernel: out[i] = in[h(i)], n = 2^k, elem_bytes 4, 8 or 16.
 cudaError_t launch_random_gather(const void *in, void *out, uint32_t k, uint32_t elem_bytes, cudaStream_t stream);
 

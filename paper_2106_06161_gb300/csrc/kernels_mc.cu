@@ -25,14 +25,6 @@ constexpr int kMcItems = 4;
 constexpr int kMcWarps = kMcBlock / 32;
 constexpr uint32_t kMcChunk = kMcBlock * kMcItems;
 
-__device__ __forceinline__ uint32_t splitmix_key(uint64_t seed, uint32_t r)
-{
-    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (static_cast<uint64_t>(r) + 1ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return static_cast<uint32_t>(z ^ (z >> 31));
-}
-
 __device__ __forceinline__ double block_sum(double v, double *s_red)
 {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -72,7 +64,7 @@ __global__ void __launch_bounds__(kMcBlock) mc_kernel(const __grid_constant__ Mc
     const double total = s_total;
 
     for (uint32_t inst = blockIdx.x; inst < a.count; inst += gridDim.x) {
-        for (uint32_t r = threadIdx.x; r < a.rounds; r += kMcBlock) s_keys[r] = splitmix_key(a.base_seed + inst, r);
+        for (uint32_t r = threadIdx.x; r < a.rounds; r += kMcBlock) s_keys[r] = dev::splitmix_key(a.base_seed + inst, r);
         __syncthreads();
         uint32_t running = 0;
         double s1 = 0.0;

@@ -121,3 +121,17 @@ def test_lcg_params_agree_with_oracle(lib):
     for seed in (0, 1, 77, 2**64 - 1):
         for n in (5, 1000, 2**20 + 1, 2**28 + 12345):
             assert bshuffle_lcg_params(seed, n) == oracle.lcg_params(seed, oracle.domain_bits(n))
+
+
+def test_shapley_argument_errors(lib):
+    from paper_2106_06161_gb300 import _lib as L
+    buf = (ctypes.c_uint64 * 64)()
+    a = ctypes.addressof(buf)
+    f = lib.bshuffle_shapley_voting
+    assert f(a, 8, 5, 0, 10, 65, a + 256, None) == L.BSHUFFLE_ERR_ROUNDS
+    assert f(None, 8, 5, 0, 10, 24, a + 256, None) == L.BSHUFFLE_ERR_NULL
+    assert f(a, 8, 5, 0, 10, 24, None, None) == L.BSHUFFLE_ERR_NULL
+    assert f(a + 2, 8, 5, 0, 10, 24, a + 256, None) == L.BSHUFFLE_ERR_ALIGN
+    assert f(a, 8, 5, 0, 10, 24, a + 260, None) == L.BSHUFFLE_ERR_ALIGN
+    assert f(a, 2**32, 5, 0, 10, 24, a + 256, None) == L.BSHUFFLE_ERR_TOO_LARGE
+    assert f(None, 0, 5, 0, 10, 24, None, None) == L.BSHUFFLE_OK

@@ -33,6 +33,8 @@ MC_SHIFT = 0.05
 MC_SHUFFLES = 10_000
 ROWS_SHAPE = (65536, 1024)
 ROWS_SEED = 7
+VOTING_PLAYERS = 10_000
+VOTING_SAMPLES = 100_000
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -97,3 +99,14 @@ def mc_samples(group: int = MC_GROUP, shift: float = MC_SHIFT, seed: int = 11) -
 def normal_rows(rows: int, cols: int, seed: int = ROWS_SEED) -> np.ndarray:
     """A [rows x cols] float32 N(0,1) matrix (cast to BF16 by the caller if needed)."""
     return _rng(seed).standard_normal((rows, cols), dtype=np.float32)
+
+
+def voting_weights(n: int = VOTING_PLAYERS, seed: int = 31) -> np.ndarray:
+    """Player weights of a weighted voting game: 1 + floor(LogNormal(2, 1)),
+    uint32 (a few heavy players among many light ones)."""
+    return (1 + np.floor(_rng(seed).lognormal(2.0, 1.0, size=n))).astype(np.uint32)
+
+
+def majority_quota(weights: np.ndarray) -> int:
+    """Simple majority of the total weight."""
+    return int(np.asarray(weights, dtype=np.int64).sum()) // 2 + 1
