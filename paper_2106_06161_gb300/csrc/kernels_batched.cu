@@ -23,8 +23,26 @@ namespace {
 
 using dev::kFull;
 
-constexpr int kBBlock = 256;
-constexpr int kBItems = 8;
+// CTA shape of the persistent kernel (overridable at build time for tuning
+// experiments): threads, domain indices per thread, and the resident CTAs
+// per SM that the register budget targets for elements of up to 4 bytes
+// (8- and 16-byte elements hold more live data and target fewer).
+#ifndef BSHUFFLE_BATCH_BLOCK
+#define BSHUFFLE_BATCH_BLOCK 256
+#endif
+#ifndef BSHUFFLE_BATCH_ITEMS
+#define BSHUFFLE_BATCH_ITEMS 8
+#endif
+#ifndef BSHUFFLE_BATCH_MIN_CTAS
+#define BSHUFFLE_BATCH_MIN_CTAS 5
+#endif
+constexpr int kBBlock = BSHUFFLE_BATCH_BLOCK;
+constexpr int kBItems = BSHUFFLE_BATCH_ITEMS;
+constexpr int kBMinCtas = BSHUFFLE_BATCH_MIN_CTAS;
+constexpr int min_ctas_for(unsigned elem_bytes)
+{
+    return elem_bytes <= 4 ? kBMinCtas : (elem_bytes == 8 ? (kBMinCtas > 3 ? 3 : kBMinCtas) : 2);
+}
 constexpr uint32_t kTile = kBBlock * kBItems;
 constexpr uint32_t kRingShift = 16;
 constexpr uint64_t kRingWords = uint64_t{1} << kRingShift;
@@ -98,12 +116,23 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const __grid_c
     }
 }
 
-// The instance owning global tile g: the largest t with tile_prefix[t] <= g.
-// Warp-cooperative: every pass splits the candidate range into 32 parts.
-__device__ __forceinline__ uint32_t find_instance(const uint64_t *prefix, uint32_t count, uint64_t g)
+// The instance owning global tile g: the largest t in [lo, hi) with
+// tile_prefix[t] <= g, given tile_prefix[lo] <= g.  Warp-cooperative.  The
+// first probe reads the 32 entries after lo (one coalesced load): a CTA's
+// successive tickets are a grid's width apart, so the owner of its next
+// ticket is usually among the next few instances.  Wider ranges are then
+// split into 32 parts per pass.
+__device__ __forceinline__ uint32_t find_instance(const uint64_t *prefix, uint32_t lo, uint32_t hi, uint64_t g)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    uint32_t lo = 0, hi = count;  // answer in [lo, hi)
+    {
+        const uint32_t m = lo + lane;
+        const bool le = m < hi && prefix[m] <= g;
+        const uint32_t ball = __ballot_sync(kFull, le);
+        const uint32_t top = 31u - static_cast<uint32_t>(__clz(ball));  // lane 0 always qualifies
+        if (top < 31u || lo + 32u >= hi) return lo + top;
+        lo += 31u;
+    }
     while (hi - lo > 32u) {
         const uint32_t span = hi - lo;
         const uint32_t m = lo + static_cast<uint32_t>((static_cast<uint64_t>(span) * lane) / 32u);
@@ -121,33 +150,90 @@ __device__ __forceinline__ uint32_t find_instance(const uint64_t *prefix, uint32
     return lo + static_cast<uint32_t>(31 - __clz(ball));
 }
 
-__device__ __forceinline__ uint32_t splitmix_key(uint64_t seed, uint32_t r)
-{
-    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (static_cast<uint64_t>(r) + 1ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return static_cast<uint32_t>(z ^ (z >> 31));
-}
-
 struct BatchJob {
     const void *in;
     void *out;
-    uint64_t first;
+    uint64_t first;  // global index of the instance's first tile
+    uint64_t end;    // one past its last tile
     Geometry g;
-    uint64_t ticket;
+    uint64_t seed;
+    uint32_t instance;
+    uint32_t ticket;
 };
 
-template <class T, bool ODD, int ITEMS>
-__device__ __forceinline__ void batch_tile(const BatchArgs &a, const BatchJob &job, const uint32_t *keys,
-                                           dev::TileShared<ITEMS *(kBBlock / 32)> &st, const dev::StatusRing &ring)
+// CTA state, double-buffered: the job of the CTA's next ticket is resolved
+// into one buffer while the tile of the other is still being stored.
+template <int ENTRIES>
+struct BatchShared {
+    dev::TileShared<ENTRIES> st[2];
+    uint32_t keys[2][kMaxRounds];
+    BatchJob job[2];
+};
+
+// Run by one full warp: turns ticket `ticket` into its job (instance,
+// geometry, round keys) in buffer `nb`.  `prev` is the job of the CTA's
+// previous ticket (null before the first one); a CTA's tickets grow, so the
+// owner is `prev`'s instance or a later one.
+template <int ENTRIES>
+__device__ __forceinline__ void resolve_job(const BatchArgs &a, uint32_t ticket, uint64_t total,
+                                            const BatchJob *prev, BatchShared<ENTRIES> &sh, int nb)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    BatchJob &job = sh.job[nb];
+    if (ticket >= total) {
+        if (lane == 0) job.ticket = ticket;
+        return;
+    }
+    uint64_t seed;
+    if (prev != nullptr && ticket < prev->end) {
+        seed = prev->seed;
+        if (lane == 0) {
+            job = *prev;
+            job.ticket = ticket;
+        }
+    } else {
+        const uint32_t lo = prev != nullptr ? prev->instance + 1u : 0u;
+        const uint32_t t = find_instance(a.tile_prefix, lo, a.count, ticket);
+        const BatchDesc d = a.descs[t];
+        const BatchPlan p = a.plan[t];
+        seed = d.seed;
+        if (lane == 0) {
+            const uint32_t k = p.k;
+            job.in = d.in;
+            job.out = d.out;
+            job.first = p.first_tile;
+            job.end = p.first_tile + p.tiles;
+            job.g.n = static_cast<uint32_t>(d.n);
+            job.g.k = k;
+            job.g.L = k / 2;
+            job.g.R = k - k / 2;
+            job.g.lmask = (1u << (k / 2)) - 1u;
+            job.g.rmask = (k - k / 2) >= 32 ? 0xffffffffu : ((1u << (k - k / 2)) - 1u);
+            job.g.domain = uint64_t{1} << k;
+            job.g.odd_mul = 1u << (31u - k / 2);
+            job.seed = d.seed;
+            job.instance = t;
+            job.ticket = ticket;
+        }
+    }
+    for (uint32_t r = lane; r < a.rounds; r += 32) sh.keys[nb][r] = dev::splitmix_key(seed, r);
+}
+
+// One tile of job `b`, then the CTA's next ticket.  The next ticket is taken
+// only after the look-back: a CTA that held a ticket while its current tile
+// still waited on other tiles would make every later tile wait for it.  Warp
+// 1 takes it and resolves it into buffer b ^ 1 while the other warps store.
+template <class T, bool ODD, int ITEMS, int ENTRIES>
+__device__ __forceinline__ void batch_tile(const BatchArgs &a, const BatchJob &job, BatchShared<ENTRIES> &sh, int b,
+                                           const dev::StatusRing &ring, uint64_t total)
 {
     constexpr int WARPS = kBBlock / 32;
-    constexpr int ENTRIES = ITEMS * WARPS;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
     const Geometry &g = job.g;
     const uint64_t tile = job.ticket;
     const uint32_t base = static_cast<uint32_t>(tile - job.first) * kTile;
+    dev::TileShared<ENTRIES> &st = sh.st[b];
 
     uint32_t left[ITEMS], right[ITEMS];
 #pragma unroll
@@ -156,7 +242,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &a, const BatchJob &j
         left[j] = i >> g.R;
         right[j] = i & g.rmask;
     }
-    dev::cipher_items<ODD, ITEMS>(left, right, keys, a.rounds, g);
+    dev::cipher_items<ODD, ITEMS>(left, right, sh.keys[b], a.rounds, g);
     uint32_t src[ITEMS];
     bool keep[ITEMS];
     T val[ITEMS];
@@ -179,6 +265,8 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &a, const BatchJob &j
     if (warp == 0)
         dev::tile_scan_lookback<ENTRIES>(st, ring, tile, job.first, a.timeout_ns, a.skip_publish_tile, a.ws);
     __syncthreads();
+    uint32_t next = 0;
+    if (threadIdx.x == 32) next = atomicAdd(&a.ws->batch_ticket, 1u);
     if (st.ok != 0u) {
         const uint32_t prefix = st.prefix;
         const uint32_t lt = dev::lanemask_lt();
@@ -192,50 +280,36 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &a, const BatchJob &j
             }
         }
     }
+    if (warp == 1) resolve_job<ENTRIES>(a, __shfl_sync(kFull, next, 0), total, &sh.job[b], sh, b ^ 1);
+    __syncthreads();
 }
 
+// Persistent CTAs, a few per SM, take tickets in order and only when they
+// are ready to start the tile, so the smallest unfinished ticket always
+// belongs to a running CTA whose look-back depends only on smaller tickets:
+// every wait ends.
 template <class T>
-__global__ void __launch_bounds__(kBBlock) batch_tile_kernel(const __grid_constant__ BatchArgs a)
+__global__ void __launch_bounds__(kBBlock, min_ctas_for(sizeof(T))) batch_tile_kernel(const __grid_constant__ BatchArgs a)
 {
     constexpr int ENTRIES = kBItems * (kBBlock / 32);
-    __shared__ dev::TileShared<ENTRIES> st;
-    __shared__ uint32_t s_keys[kMaxRounds];
-    __shared__ BatchJob s_job;
+    __shared__ BatchShared<ENTRIES> sh;
     const dev::StatusRing ring{a.status, kRingWords - 1, kRingShift, 1u};
     const uint64_t total = *reinterpret_cast<volatile const uint64_t *>(a.total_tiles);
+    const uint32_t warp = threadIdx.x >> 5;
 
-    while (true) {
-        if (threadIdx.x == 0) s_job.ticket = atomicAdd(&a.ws->batch_ticket, 1u);
-        __syncthreads();
-        const uint64_t ticket = s_job.ticket;
-        if (ticket >= total) break;
-        if (threadIdx.x < 32) {
-            const uint32_t t = find_instance(a.tile_prefix, a.count, ticket);
-            if (threadIdx.x == 0) {
-                const BatchDesc d = a.descs[t];
-                const uint32_t k = a.plan[t].k;
-                s_job.in = d.in;
-                s_job.out = d.out;
-                s_job.first = a.plan[t].first_tile;
-                s_job.g.n = static_cast<uint32_t>(d.n);
-                s_job.g.k = k;
-                s_job.g.L = k / 2;
-                s_job.g.R = k - k / 2;
-                s_job.g.lmask = (1u << (k / 2)) - 1u;
-                s_job.g.rmask = (k - k / 2) >= 32 ? 0xffffffffu : ((1u << (k - k / 2)) - 1u);
-                s_job.g.domain = uint64_t{1} << k;
-                s_job.g.odd_mul = 1u << (31u - k / 2);
-            }
-            const uint64_t seed = __shfl_sync(kFull, threadIdx.x == 0 ? a.descs[t].seed : 0ull, 0);
-            for (uint32_t r = threadIdx.x; r < a.rounds; r += 32) s_keys[r] = splitmix_key(seed, r);
-        }
-        __syncthreads();
-        const BatchJob job = s_job;
+    if (warp == 1) {
+        uint32_t t0 = 0;
+        if ((threadIdx.x & 31u) == 0) t0 = atomicAdd(&a.ws->batch_ticket, 1u);
+        resolve_job<ENTRIES>(a, __shfl_sync(kFull, t0, 0), total, nullptr, sh, 0);
+    }
+    __syncthreads();
+    for (int b = 0;; b ^= 1) {
+        const BatchJob job = sh.job[b];
+        if (job.ticket >= total) break;
         if (job.g.k & 1u)
-            batch_tile<T, true, kBItems>(a, job, s_keys, st, ring);
+            batch_tile<T, true, kBItems, ENTRIES>(a, job, sh, b, ring, total);
         else
-            batch_tile<T, false, kBItems>(a, job, s_keys, st, ring);
-        __syncthreads();
+            batch_tile<T, false, kBItems, ENTRIES>(a, job, sh, b, ring, total);
     }
     if (threadIdx.x == 0) {
         __threadfence();
