@@ -47,8 +47,8 @@ ELEM = 8
 SEED = 0
 ROUNDS = 24
 METRIC = "shuffled elements/s at n=2^28 uint64 (VariablePhilox bijective shuffle)"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_permute_u64_2p28.json")
-STRATEGIES = {"auto": 0, "single_pass": 1, "staged": 2}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_full_size_launches.json")
+STRATEGIES = {"auto": 0, "single_pass": 1, "staged": 2, "pipelined": 3}
 
 
 def parse():
@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
-    p.add_argument("--strategy", choices=["auto", "single_pass", "staged"], default="auto",
+    p.add_argument("--strategy", choices=["auto", "single_pass", "staged", "pipelined"], default="auto",
                    help="how bshuffle_permute moves data (identical output)")
     p.add_argument("--profile-batched", type=int, default=0,
                    help="only run warmup + steps batched launches over this many instances (for ncu)")
@@ -148,6 +148,12 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def job_value(n_per_rank: int, world: int, steps: int, region_ms: float) -> float:
+    """Whole-job elements/s: every rank shuffles its own n per step (weak
+    scaling), over the slowest rank's timed region."""
+    return n_per_rank * world * steps / (region_ms * 1e-3)
 
 
 def max_over_ranks(value: float, world: int) -> float:
@@ -240,12 +246,14 @@ FORWARD_OPS_PER_EVAL = 24 * 5
 INVERSE_OPS_PER_EVAL = 24 * 7
 
 
-def roofline_for(passes, bsbuild):
+def roofline_for(passes, bsbuild, strategy):
     """Roofline of the dominant kernel of one step, plus every pass's line."""
     peak, peak_kind = measured_peaks()
     n, k = N_MAIN, 28
-    if len(passes) == 1:
+    if len(passes) == 1 and strategy == STRATEGIES["single_pass"]:
         names = [("elem_tile_kernel<uint64, Gather, even k>", "kernels_elem.cu", "hbm", 2 * n * ELEM, None)]
+    elif len(passes) == 1:
+        names = [("pipe_tile_kernel<uint64, even k>", "kernels_pipe.cu", "hbm", 2 * n * ELEM, None)]
     else:
         names = [("staged_bucket_kernel<uint64, even k>", "kernels_staged.cu", "alu", 2**k, n * (ELEM + ELEM + 4)),
                  ("staged_scatter_kernel<uint64>", "kernels_staged.cu", "hbm", n * (ELEM + 4 + ELEM), None)]
@@ -318,7 +326,7 @@ def run_ours(args):
         raise SystemExit("device error during the timed region")
     region_ms = max_over_ranks(region_ms, world)
     ms_per_step = region_ms / args.steps
-    value = N_MAIN * world * args.steps / (region_ms * 1e-3)
+    value = job_value(N_MAIN, world, args.steps, region_ms)
 
     # per-kernel durations, live: the same step with the library's per-pass
     # CUDA events on this stream, read back after every step
@@ -330,7 +338,7 @@ def run_ours(args):
         pass_ms.append(bs.bshuffle_last_pass_ms(sptr))
     bs.bshuffle_set_pass_timing(False)
     passes = [statistics.mean(col) for col in zip(*pass_ms)]
-    roofline, pass_lines = roofline_for(passes, bsbuild)
+    roofline, pass_lines = roofline_for(passes, bsbuild, bs.bshuffle_get_strategy())
 
     e2e = e2e_pipeline(bs, torch, dev, host, seed, args, world)
     # the round trip is exact
@@ -375,7 +383,7 @@ def run_ours(args):
                        "l2": "inputs (2 GiB) larger than L2, no flush",
                        "parallelism": f"independent shuffles, {world} GPU(s)"},
             "logical_gbps": 2 * N_MAIN * ELEM / (ms_per_step * 1e-3) / 1e9,
-            "strategy": {0: "auto", 1: "single_pass", 2: "staged"}[bs.bshuffle_get_strategy()],
+            "strategy": {0: "auto", 1: "single_pass", 2: "staged", 3: "pipelined"}[bs.bshuffle_get_strategy()],
             "kernels_per_step": len(passes), "roofline": roofline, "passes": pass_lines,
             "single_pass_tuning": tuning,
             "e2e": e2e, "gpu_launches": args.steps * len(passes), "clocks": clk,
@@ -449,7 +457,7 @@ def secondary(bs, torch, dev, stream):
     """Worst-case padding and the uneven batch (one-off measurements)."""
     out = {}
     sptr = stream.cuda_stream
-    # both strategies at n = 2^28 and at n = 2^28 + 12345 (domain 2^29, about
+    # every strategy at n = 2^28 and at n = 2^28 + 12345 (domain 2^29, about
     # half of the images dropped: the paper's worst case)
     for label, n_, seed_ in (("2p28_u64", N_MAIN, 0), ("worst_case_2p28_plus_12345_u64", N_WORST, 1)):
         host = workloads.uniform_u64(n_, seed_)
@@ -457,7 +465,8 @@ def secondary(bs, torch, dev, stream):
         y = torch.empty_like(x)
         xp, yp = x.data_ptr(), y.data_ptr()
         f = lambda: bs.bshuffle_permute(xp, yp, n_, ELEM, seed_, ROUNDS, sptr)  # noqa: E731
-        for name, strat in (("single_pass", bs.BSHUFFLE_STRATEGY_SINGLE_PASS), ("staged", bs.BSHUFFLE_STRATEGY_STAGED)):
+        for name, strat in (("single_pass", bs.BSHUFFLE_STRATEGY_SINGLE_PASS),
+                            ("pipelined", bs.BSHUFFLE_STRATEGY_PIPELINED), ("staged", bs.BSHUFFLE_STRATEGY_STAGED)):
             bs.bshuffle_set_strategy(strat)
             for _ in range(3):
                 f()
@@ -477,7 +486,7 @@ def secondary(bs, torch, dev, stream):
         y = torch.empty_like(x)
         xp, yp = x.data_ptr(), y.data_ptr()
         row = {}
-        for variant, name in ((0, "bijective0"), (1, "bijective1"), (2, "bijective2")):
+        for variant, name in ((0, "bijective0"), (1, "bijective1"), (2, "bijective2"), (3, "bijective2_pipelined")):
             f = lambda: bs.bshuffle_permute_ablation(xp, yp, n_, ELEM, 3, ROUNDS, variant, sptr)  # noqa: E731
             for _ in range(3):
                 f()

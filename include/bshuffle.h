@@ -167,6 +167,9 @@ int bshuffle_lcg_params(uint64_t seed, uint64_t n, uint64_t *a, uint64_t *c);
  *              and a second pass evaluates f again, ranks and gathers.
  *   variant 2  "Bijective2": the fused single pass (as bshuffle_permute
  *              with BSHUFFLE_STRATEGY_SINGLE_PASS).
+ *   variant 3  the fused single pass with its look-back taken off the
+ *              compute warps (as bshuffle_permute with
+ *              BSHUFFLE_STRATEGY_PIPELINED); not in the paper.
  * Scratch lives in the stream's workspace.  elem_bytes 4, 8 or 16.
  */
 int bshuffle_permute_ablation(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
@@ -273,14 +276,23 @@ int bshuffle_release_workspaces(void);
  *       while it is resident in L2.  Random HBM accesses are rate-limited on
  *       GB300, streaming ones are not.  Workspace n * (4 + elem_bytes) bytes
  *       plus a little, allocated on first use per stream.
+ *   BSHUFFLE_STRATEGY_PIPELINED  the single pass for 4, 8 and 16-byte
+ *       elements (other widths run BSHUFFLE_STRATEGY_SINGLE_PASS) with its
+ *       look-back taken off the compute warps: persistent CTAs gather each
+ *       tile into shared memory with cp.async while one warp per CTA ranks,
+ *       looks back and stores the previous tile.  Same memory traffic and
+ *       workspace as the single pass.
  *   BSHUFFLE_STRATEGY_AUTO (default)  staged when it applies and
- *       n * elem_bytes >= 256 MiB, else single pass; if the staged workspace
- *       cannot be allocated the single pass runs instead.
+ *       n * elem_bytes >= 256 MiB; otherwise the pipelined single pass for 4
+ *       and 8-byte elements and the plain single pass for other widths; if
+ *       the staged workspace cannot be allocated the single pass runs
+ *       instead.
  * The setting is process-wide.  Returns BSHUFFLE_ERR_INVALID for other values.
  */
 #define BSHUFFLE_STRATEGY_AUTO 0
 #define BSHUFFLE_STRATEGY_SINGLE_PASS 1
 #define BSHUFFLE_STRATEGY_STAGED 2
+#define BSHUFFLE_STRATEGY_PIPELINED 3
 int bshuffle_set_strategy(int strategy);
 int bshuffle_get_strategy(void);
 

@@ -49,6 +49,7 @@ from ._lib import (
     BSHUFFLE_STRATEGY_AUTO,
     BSHUFFLE_STRATEGY_SINGLE_PASS,
     BSHUFFLE_STRATEGY_STAGED,
+    BSHUFFLE_STRATEGY_PIPELINED,
     bshuffle_version,
     error_string,
     load,
@@ -63,7 +64,7 @@ __all__ = [
     "bshuffle_get_strategy", "bshuffle_set_pass_timing", "bshuffle_last_pass_ms",
     "bshuffle_tuning_configs", "bshuffle_tuning_select", "bshuffle_tuning_selected",
     "bshuffle_permute_lcg", "bshuffle_lcg_params", "permute_lcg", "bshuffle_permute_ablation", "BSHUFFLE_STRATEGY_AUTO", "BSHUFFLE_STRATEGY_SINGLE_PASS",
-    "BSHUFFLE_STRATEGY_STAGED",
+    "BSHUFFLE_STRATEGY_STAGED", "BSHUFFLE_STRATEGY_PIPELINED",
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
     "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",
     "bshuffle_shapley_voting", "shapley_voting",

@@ -28,6 +28,7 @@ BSHUFFLE_ERR_INVALID = -10
 BSHUFFLE_STRATEGY_AUTO = 0
 BSHUFFLE_STRATEGY_SINGLE_PASS = 1
 BSHUFFLE_STRATEGY_STAGED = 2
+BSHUFFLE_STRATEGY_PIPELINED = 3
 DEFAULT_ROUNDS = 24
 MAX_ROUNDS = 64
 MAX_N = 2**32 - 1

@@ -206,8 +206,11 @@ cudaEvent_t *timing_marks(Workspace *ws)
 }
 
 // One fused launch over the whole domain of n.
+// Which single-pass kernel run_fused launches for a gather.
+enum class FusedKernel { ByStrategy, Plain, Pipelined };
+
 int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed, uint32_t rounds,
-              Mode mode, void *stream_ptr)
+              Mode mode, void *stream_ptr, FusedKernel which = FusedKernel::ByStrategy)
 {
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
     TileArgs a{};
@@ -220,8 +223,17 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     a.timeout_ns = g_timeout_ns.load();
     fill_keys(seed, rounds, a.keys);
     const bool rows = (mode == Mode::Gather || mode == Mode::Scatter) && elem_bytes > 16;
+    // the pipelined kernel: on request for 4, 8 and 16-byte elements, and by
+    // default for 4 and 8-byte elements (the plain kernel is faster for 16)
+    const int strategy = g_strategy.load();
+    const bool pipe_width = elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 16;
+    const bool pipe =
+        mode == Mode::Gather && pipe_width &&
+        (which == FusedKernel::Pipelined ||
+         (which == FusedKernel::ByStrategy &&
+          (strategy == BSHUFFLE_STRATEGY_PIPELINED || (strategy == BSHUFFLE_STRATEGY_AUTO && elem_bytes != 16))));
     const int config = rows ? 0 : bsh::elem_config_for(elem_bytes, mode, rounds);
-    const uint64_t tile = rows ? bsh::rows_tile_size() : bsh::elem_tile_size(config);
+    const uint64_t tile = rows ? bsh::rows_tile_size() : (pipe ? bsh::pipe_tile_size(elem_bytes) : bsh::elem_tile_size(config));
     const uint64_t tiles = (a.g.domain + tile - 1) / tile;
     a.num_tiles = static_cast<uint32_t>(tiles);
     Workspace *ws = nullptr;
@@ -231,8 +243,9 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     a.status = ws->status();
     cudaEvent_t *marks = mode == Mode::Gather ? timing_marks(ws) : nullptr;
     if (marks != nullptr && cudaEventRecord(marks[0], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
-    const cudaError_t e =
-        rows ? bsh::launch_rows(a, mode, stream) : bsh::launch_elem(a, mode, elem_bytes, config, stream);
+    const cudaError_t e = rows   ? bsh::launch_rows(a, mode, stream)
+                          : pipe ? bsh::launch_pipe(a, elem_bytes, stream)
+                                 : bsh::launch_elem(a, mode, elem_bytes, config, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     if (marks != nullptr) {
         if (cudaEventRecord(marks[1], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
@@ -365,7 +378,8 @@ int bshuffle_permute(const void *in, void *out, uint64_t n, uint32_t elem_bytes,
     rc = check_buffers(in, out, n, elem_bytes);
     if (rc != BSHUFFLE_OK) return rc;
     const int strategy = g_strategy.load();
-    if (strategy != BSHUFFLE_STRATEGY_SINGLE_PASS && staged_eligible(n, elem_bytes) &&
+    if (strategy != BSHUFFLE_STRATEGY_SINGLE_PASS && strategy != BSHUFFLE_STRATEGY_PIPELINED &&
+        staged_eligible(n, elem_bytes) &&
         (strategy == BSHUFFLE_STRATEGY_STAGED || n * elem_bytes >= kStagedMinBytes)) {
         rc = run_staged(in, out, n, elem_bytes, seed, rounds, stream);
         if (rc == BSHUFFLE_OK || strategy == BSHUFFLE_STRATEGY_STAGED) return rc;
@@ -465,11 +479,13 @@ int bshuffle_permute_ablation(const void *in, void *out, uint64_t n, uint32_t el
     int rc = check_common(n, rounds);
     if (rc != BSHUFFLE_OK) return rc;
     if (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16) return BSHUFFLE_ERR_ELEM;
-    if (variant < 0 || variant > 2) return BSHUFFLE_ERR_INVALID;
+    if (variant < 0 || variant > 3) return BSHUFFLE_ERR_INVALID;
     if (n == 0) return BSHUFFLE_OK;
     rc = check_buffers(in, out, n, elem_bytes);
     if (rc != BSHUFFLE_OK) return rc;
-    if (variant == 2) return run_fused(in, out, n, elem_bytes, seed, rounds, Mode::Gather, stream_ptr);
+    if (variant >= 2)
+        return run_fused(in, out, n, elem_bytes, seed, rounds, Mode::Gather, stream_ptr,
+                         variant == 2 ? FusedKernel::Plain : FusedKernel::Pipelined);
 
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
     bsh::AblationArgs a{};
@@ -699,7 +715,7 @@ int bshuffle_release_workspaces(void)
 int bshuffle_set_strategy(int strategy)
 {
     if (strategy != BSHUFFLE_STRATEGY_AUTO && strategy != BSHUFFLE_STRATEGY_SINGLE_PASS &&
-        strategy != BSHUFFLE_STRATEGY_STAGED)
+        strategy != BSHUFFLE_STRATEGY_STAGED && strategy != BSHUFFLE_STRATEGY_PIPELINED)
         return BSHUFFLE_ERR_INVALID;
     g_strategy.store(strategy);
     return BSHUFFLE_OK;

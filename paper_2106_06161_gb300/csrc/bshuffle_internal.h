@@ -203,6 +203,10 @@ struct McArgs {
 
 cudaError_t launch_mc(const McArgs &a, cudaStream_t stream);
 
+// Pipelined single pass (gather, 4/8/16-byte elements): tile size and launch.
+uint32_t pipe_tile_size(uint32_t elem_bytes);
+cudaError_t launch_pipe(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream);
+
 struct ShapleyArgs {
     const uint32_t *w;  // player weights
     uint64_t *counts;   // pivot counts per player, zeroed by the caller

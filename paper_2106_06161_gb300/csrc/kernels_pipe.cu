@@ -1,0 +1,338 @@
+// Pipelined single pass of Algorithm 1 (gather mode, 4-, 8- and 16-byte
+// elements): the same output as the fused tile kernel, with the inter-tile
+// look-back taken off the compute warps' path.
+//
+// In the plain fused kernel every warp of a tile waits while one warp looks
+// back, and under a full load of random gathers a look-back takes several
+// L2 round trips.  Here a persistent CTA holds NCW compute warps and one
+// look-back warp, and the compute warps run one tile ahead of their stores:
+//
+//   compute warps, iteration i (buffer i % 2): take a ticket, evaluate the
+//     bijection, start copying the kept elements X[f(i)] into the buffer
+//     with cp.async (one copy group per thread and tile), store the keep
+//     ballots and publish the tile aggregate (the last compute warp to add
+//     its count does it); then store tile i - 1: wait for its rank (look-back
+//     warp) and for this thread's own copy group of that tile, and write each
+//     element this thread gathered to its slot.
+//   look-back warp, tile i: wait for the ballots, form the in-tile offsets,
+//     look back, publish the inclusive prefix and hand the prefix to the
+//     compute warps.
+//
+// Tickets stay in order of readiness: a tile's aggregate is published by the
+// compute warps right after its ballots, never after another tile's
+// look-back, and the compute warps wait for a rank only after that.  The
+// smallest unfinished ticket therefore always makes progress.  Every wait is
+// bounded.
+#include <cstdint>
+
+#include "bshuffle_device.cuh"
+#include "bshuffle_internal.h"
+
+namespace bsh {
+namespace {
+
+using dev::kFull;
+
+// Shape of the persistent CTA (overridable at build time for tuning
+// experiments): compute warps, domain indices per compute thread for 16-byte
+// elements (others take 8), and the resident CTAs per SM that the register
+// budget targets.  Three CTAs per SM measured fastest: more tiles in flight
+// lengthen every look-back walk.
+#ifndef BSHUFFLE_PIPE_ITEMS16
+#define BSHUFFLE_PIPE_ITEMS16 8
+#endif
+#ifndef BSHUFFLE_PIPE_MIN_CTAS
+#define BSHUFFLE_PIPE_MIN_CTAS 3
+#endif
+constexpr int kPipeComputeWarps = 8;
+constexpr int pipe_items(uint32_t elem_bytes) { return elem_bytes >= 16 ? BSHUFFLE_PIPE_ITEMS16 : 8; }
+constexpr uint32_t pipe_tile(uint32_t elem_bytes) { return kPipeComputeWarps * 32 * pipe_items(elem_bytes); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 state;\n\t"
+        "mbarrier.arrive.shared.b64 state, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+// Waits for the completion of the barrier phase of parity `parity`; gives up
+// (false) after `limit_ns` or when another role has raised `abort`.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                          const volatile uint32_t *abort)
+{
+    uint64_t start = 0;
+    uint32_t spins = 0;
+    while (!mbar_test(bar, parity)) {
+        if (*abort != 0u) return false;
+        const uint64_t now = dev::global_ns();
+        if (start == 0) {
+            start = now;
+        } else if (now - start > limit_ns || ++spins > (1u << 26)) {
+            return false;
+        }
+    }
+    return true;
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src)
+{
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst_smem)), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Waits until every copy group of this thread but the most recent one has landed.
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Barrier 1 over the compute warps only.
+__device__ __forceinline__ void compute_sync(uint32_t threads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
+}
+
+template <int NCW, int ITEMS>
+struct PipeShared {
+    static constexpr int E = NCW * ITEMS;
+    uint64_t full[2];            // compute -> look-back: ballots of the buffer's tile written
+    uint64_t ranked[2];          // look-back -> compute: offsets and prefix of that tile ready
+    unsigned long long aggc[2];  // (compute warps done << 32) | kept count, per buffer
+    uint32_t masks[2][E];        // keep ballot per (item, compute warp)
+    uint32_t offs[2][E];         // exclusive in-tile offsets
+    uint32_t prefix[2];          // exclusive prefix of the tile over all earlier tiles
+    uint32_t ok[2];              // look-back finished in time
+    uint32_t ticket[2];
+    uint32_t tag;
+    uint32_t abort;
+};
+
+template <class T, bool ODD, int NCW, int ITEMS>
+__global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_tile_kernel(const __grid_constant__ TileArgs a)
+{
+    constexpr uint32_t NCT = NCW * 32;  // compute threads
+    constexpr uint32_t TILE = NCT * ITEMS;
+    constexpr int E = NCW * ITEMS;
+    __shared__ PipeShared<NCW, ITEMS> sh;
+    extern __shared__ __align__(16) unsigned char pipe_dyn[];
+    T *vals = reinterpret_cast<T *>(pipe_dyn);  // [2][TILE], natural (item, thread) order
+
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    // a wait for the other role gets room for one full look-back timeout
+    const uint64_t role_limit = 2 * a.timeout_ns + 1000000000ull;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh.full[b], NCW);
+            mbar_init(&sh.ranked[b], 1);
+            sh.aggc[b] = 0ull;
+        }
+        sh.tag = dev::ld_relaxed_gpu(&a.ws->tag);
+        sh.abort = 0u;
+    }
+    __syncthreads();
+    const uint32_t tag = sh.tag;
+    const dev::StatusRing ring{a.status, ~0ull, 63u, tag};
+    volatile uint32_t *abort = &sh.abort;
+
+    if (warp < NCW) {
+        // ---------------------------------------------------------- compute
+        const uint32_t ct = threadIdx.x;
+        const uint32_t lt = dev::lanemask_lt();
+        const T *in = static_cast<const T *>(a.in);
+        T *out = static_cast<T *>(a.out);
+        for (uint32_t iter = 0;; ++iter) {
+            const int b = static_cast<int>(iter & 1u);
+            if (ct == 0) sh.ticket[b] = *abort == 0u ? atomicAdd(&a.ws->ticket, 1u) : 0xffffffffu;
+            compute_sync(NCT);
+            const uint32_t tile = sh.ticket[b];
+            const bool stop = tile >= a.num_tiles;
+            if (!stop) {
+                const uint32_t base = tile * TILE;
+                uint32_t left[ITEMS], right[ITEMS];
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) {
+                    const uint32_t i = base + static_cast<uint32_t>(j) * NCT + ct;
+                    left[j] = i >> a.g.R;
+                    right[j] = i & a.g.rmask;
+                }
+                dev::cipher_items<ODD, ITEMS>(left, right, a.keys, a.rounds, a.g);
+                T *buf = vals + static_cast<size_t>(b) * TILE;
+                uint32_t count = 0;
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) {
+                    const uint32_t i = base + static_cast<uint32_t>(j) * NCT + ct;
+                    const uint32_t src = (left[j] << a.g.R) | right[j];
+                    const bool keep = static_cast<uint64_t>(i) < a.g.domain && src < a.g.n;
+                    if (keep) cp_async<sizeof(T)>(buf + static_cast<uint32_t>(j) * NCT + ct, in + src);
+                    const uint32_t m = __ballot_sync(kFull, keep);
+                    count += __popc(m);
+                    if (lane == 0) sh.masks[b][j * NCW + warp] = m;
+                }
+                if (lane == 0) {
+                    const unsigned long long v = atomicAdd(&sh.aggc[b], (1ull << 32) | count);
+                    if ((v >> 32) == NCW - 1 && static_cast<int64_t>(tile) != a.skip_publish_tile) {
+                        const uint32_t total = static_cast<uint32_t>(v) + count;
+                        dev::st_relaxed_gpu(ring.slot(tile), dev::status_word(tag, tile == 0u, total));
+                    }
+                }
+            }
+            cp_async_commit();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.full[b]);
+            if (iter > 0) {
+                // store the previous tile (buffer b ^ 1) once it is ranked
+                const int pb = b ^ 1;
+                const bool ranked = mbar_wait(&sh.ranked[pb], ((iter - 1u) >> 1) & 1u, role_limit, abort);
+                if (!ranked) {
+                    if (lane == 0) dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
+                    *abort = 1u;
+                }
+                cp_async_wait_prior();  // this thread's copies of the previous tile have landed
+                if (ranked && sh.ok[pb] != 0u) {
+                    const T *pbuf = vals + static_cast<size_t>(pb) * TILE;
+                    const uint32_t prefix = sh.prefix[pb];
+#pragma unroll
+                    for (int j = 0; j < ITEMS; ++j) {
+                        const uint32_t e = static_cast<uint32_t>(j) * NCW + warp;
+                        const uint32_t m = sh.masks[pb][e];
+                        if ((m >> lane) & 1u) {
+                            const uint32_t dst = prefix + sh.offs[pb][e] + __popc(m & lt);
+                            if (dst < a.g.n) out[dst] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
+                            else dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
+                        }
+                    }
+                }
+            }
+            if (stop) break;
+        }
+        cp_async_wait_all();
+    } else {
+        // -------------------------------------------------------- look-back
+        for (uint32_t iter = 0;; ++iter) {
+            const int b = static_cast<int>(iter & 1u);
+            const uint32_t parity = (iter >> 1) & 1u;
+            // lane 0 waits, so that the warp leaves the loop as one
+            bool full = false;
+            if (lane == 0) {
+                full = mbar_wait(&sh.full[b], parity, role_limit, abort);
+                if (!full) {
+                    dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
+                    *abort = 1u;
+                }
+            }
+            if (!__shfl_sync(kFull, full, 0)) break;
+            (void)mbar_test(&sh.full[b], parity);  // completed phase: every lane acquires it
+            const uint32_t tile = sh.ticket[b];
+            if (tile >= a.num_tiles) break;
+            constexpr int C = (E + 31) / 32;
+            uint32_t local[C];
+            uint32_t sum = 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int e = static_cast<int>(lane) * C + c;
+                local[c] = e < E ? static_cast<uint32_t>(__popc(sh.masks[b][e])) : 0u;
+                sum += local[c];
+            }
+            const uint32_t incl = dev::warp_inclusive_scan(sum);
+            uint32_t run = incl - sum;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int e = static_cast<int>(lane) * C + c;
+                if (e < E) sh.offs[b][e] = run;
+                run += local[c];
+            }
+            const uint32_t aggregate = __shfl_sync(kFull, incl, 31);
+            uint32_t prefix = 0;
+            bool ok = true;
+            if (tile > 0u) {
+                prefix = dev::lookback(ring, tile, 0, a.timeout_ns, ok);
+                if (lane == 0 && static_cast<int64_t>(tile) != a.skip_publish_tile)
+                    dev::st_relaxed_gpu(ring.slot(tile), dev::status_word(tag, true, prefix + aggregate));
+                if (lane == 0 && !ok) dev::record_error(a.ws, dev::kErrLookbackTimeout, tile);
+            }
+            if (lane == 0) {
+                sh.prefix[b] = prefix;
+                sh.ok[b] = ok ? 1u : 0u;
+                sh.aggc[b] = 0ull;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.ranked[b]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) dev::finish_launch(a.ws, tag, gridDim.x);
+}
+
+template <class T>
+cudaError_t launch_typed(const TileArgs &a, cudaStream_t stream)
+{
+    constexpr int NCW = kPipeComputeWarps, ITEMS = pipe_items(sizeof(T));
+    constexpr int THREADS = (NCW + 1) * 32;
+    constexpr size_t DYN = sizeof(T) * 2 * pipe_tile(sizeof(T));
+    static int per_sm[64][2] = {};
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    const bool odd = (a.g.k & 1u) != 0u;
+    auto kernel = odd ? pipe_tile_kernel<T, true, NCW, ITEMS> : pipe_tile_kernel<T, false, NCW, ITEMS>;
+    int &ctas = per_sm[device][odd ? 1 : 0];
+    if (ctas == 0) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(DYN));
+        if (e != cudaSuccess) return e;
+        int blocks = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, THREADS, DYN);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return e;
+        ctas = (blocks > 0 ? blocks : 1) * sms;
+    }
+    const uint32_t grid = a.num_tiles < static_cast<uint32_t>(ctas) ? a.num_tiles : static_cast<uint32_t>(ctas);
+    kernel<<<grid, THREADS, DYN, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t pipe_tile_size(uint32_t elem_bytes) { return pipe_tile(elem_bytes); }
+
+cudaError_t launch_pipe(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream)
+{
+    switch (elem_bytes) {
+    case 4: return launch_typed<unsigned int>(a, stream);
+    case 8: return launch_typed<unsigned long long>(a, stream);
+    case 16: return launch_typed<uint4>(a, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bsh

@@ -244,7 +244,7 @@ def test_lcg_variant_matches_oracle(width):
         assert np.array_equal(to_host(y, x), want), n
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_fusion_ablation_variants_match_oracle(variant):
     # Sec. 6: Bijective0 (separate passes), Bijective1 (two-pass scan) and
     # Bijective2 (single pass) compute the same shuffle.

@@ -1,0 +1,118 @@
+"""The pipelined single pass (BSHUFFLE_STRATEGY_PIPELINED) against the
+oracle: the same output as Algorithm 1, bit for bit, for 4-, 8- and 16-byte
+elements, small sizes with ragged last tiles up to the full worst-case
+length, plus its bounded waits and the widths it hands to the plain kernel."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from tests.gpu_helpers import assert_no_device_error, to_device, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_2106_06161_gb300 import build
+    build.build()
+    import paper_2106_06161_gb300
+    paper_2106_06161_gb300.load()
+    paper_2106_06161_gb300.bshuffle_set_strategy(paper_2106_06161_gb300.BSHUFFLE_STRATEGY_PIPELINED)
+    yield paper_2106_06161_gb300
+    paper_2106_06161_gb300.bshuffle_set_strategy(paper_2106_06161_gb300.BSHUFFLE_STRATEGY_AUTO)
+
+
+def _payload(n, width, seed):
+    rng = np.random.default_rng(seed * 31 + width)
+    if width in (1, 2, 4, 8):
+        dt = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[width]
+        return rng.integers(0, np.iinfo(dt).max, size=n, dtype=dt, endpoint=True)
+    return rng.integers(0, 256, size=(n, width), dtype=np.uint8)
+
+
+def _gpu(bs, x, seed, rounds=24):
+    y = bs.permute(to_device(x), seed, rounds)
+    assert_no_device_error()
+    return to_host(y, x)
+
+
+@pytest.mark.parametrize("width", [4, 8, 16])
+def test_matches_oracle(bs, width):
+    for n in (1, 2, 5, 17, 2047, 2048, 2049, 4097, 65537, 123457, 1_000_003):
+        for seed in (0, 9):
+            x = _payload(n, width, seed)
+            assert np.array_equal(_gpu(bs, x, seed), oracle.permute(x, seed)), (n, seed)
+
+
+@pytest.mark.parametrize("rounds", [0, 1, 24, 64])
+def test_rounds(bs, rounds):
+    for n in (33, 300_001):
+        x = _payload(n, 8, rounds)
+        assert np.array_equal(_gpu(bs, x, 5, rounds), oracle.permute(x, 5, rounds))
+
+
+def test_other_widths_use_the_plain_kernel(bs):
+    for width in (1, 2, 32):
+        x = _payload(10_007, width, 1)
+        assert np.array_equal(_gpu(bs, x, 2), oracle.permute(x, 2))
+
+
+def test_many_tiles_per_cta(bs):
+    # 2^24 + 1: 8,192 tiles, several per persistent CTA, both buffers cycling
+    for width in (4, 16):
+        x = workloads.sweep_payload(2**24 + 1, width, 3)
+        assert np.array_equal(_gpu(bs, x, 3), oracle.permute(x, 3))
+
+
+def test_full_size_worst_case_sampled(bs):
+    n, seed = 2**28 + 12345, 0
+    want = oracle.indices(n, seed)
+    x = workloads.uniform_u64(n, seed)
+    y = bs.permute(to_device(x), seed)
+    assert_no_device_error()
+    rng = np.random.default_rng(4)
+    js = np.concatenate([np.arange(4096), rng.integers(0, n, 400_000), np.arange(n - 4096, n)])
+    got = y[torch.from_numpy(js).cuda()].cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, x[want[js].astype(np.int64)])
+    # and slot for slot equal to the plain single pass
+    bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_SINGLE_PASS)
+    try:
+        y1 = bs.permute(to_device(x), seed)
+        assert_no_device_error()
+    finally:
+        bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_PIPELINED)
+    assert torch.equal(y, y1)
+
+
+def test_repeated_calls_and_streams(bs):
+    x = _payload(500_009, 8, 2)
+    want = oracle.permute(x, 11)
+    for _ in range(4):
+        assert np.array_equal(_gpu(bs, x, 11), want)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        y = bs.permute(to_device(x), 11)
+        s.synchronize()
+        assert bs.get_error() == 0
+    assert np.array_equal(to_host(y, x), want)
+
+
+def test_withheld_tile_times_out_and_recovers(bs):
+    from paper_2106_06161_gb300 import _lib as L
+    n = 40_000                      # domain 2^16: 32 tiles of 2,048 indices
+    x = torch.arange(n, dtype=torch.int64, device="cuda")
+    bs.bshuffle_set_lookback_timeout_ns(50_000_000)
+    bs.bshuffle_debug_skip_publish(3)
+    try:
+        bs.permute(x, 3)
+        torch.cuda.synchronize()
+        code = bs.get_error()
+    finally:
+        bs.bshuffle_debug_skip_publish(-1)
+        bs.bshuffle_set_lookback_timeout_ns(2_000_000_000)
+    assert code == L.BSHUFFLE_ERR_LOOKBACK_TIMEOUT
+    y = bs.permute(x, 3)
+    assert bs.get_error() == 0
+    assert np.array_equal(y.cpu().numpy(), oracle.permute(np.arange(n, dtype=np.int64), 3))
