@@ -263,30 +263,34 @@ int bshuffle_round_keys(uint64_t seed, uint32_t rounds, uint32_t *keys);
 int bshuffle_release_workspaces(void);
 
 /*
- * How bshuffle_permute moves data (the output is identical either way):
+ * How bshuffle_permute, bshuffle_inverse and bshuffle_indices move data
+ * (the output is identical either way):
  *   BSHUFFLE_STRATEGY_SINGLE_PASS  one fused launch: bijection, scan with
  *       decoupled look-back, one random read and one coalesced write per
  *       element (the paper's "Bijective2", Sec. 6).  No extra memory beyond
  *       the small workspace.
  *   BSHUFFLE_STRATEGY_STAGED  for n = 2^k >= 4096 and 4, 8 or 16-byte
  *       elements (other calls run the single pass): nothing is dropped, so
- *       element b belongs in slot f^-1(b) (the inverse cipher of Sec. 3.2).
+ *       element b belongs in slot f^-1(b) (the inverse cipher of Sec. 3.2;
+ *       bshuffle_inverse uses the same passes with slot f(b)).
  *       Pass 1 reads the input sequentially, inverts the cipher and buckets
  *       (value, slot) by 8 MiB output window; pass 2 scatters each window
  *       while it is resident in L2.  Random HBM accesses are rate-limited on
  *       GB300, streaming ones are not.  Workspace n * (4 + elem_bytes) bytes
  *       plus a little, allocated on first use per stream.
- *   BSHUFFLE_STRATEGY_PIPELINED  the single pass for 4, 8 and 16-byte
- *       elements (other widths run BSHUFFLE_STRATEGY_SINGLE_PASS) with its
- *       look-back taken off the compute warps: persistent CTAs gather each
- *       tile into shared memory with cp.async while one warp per CTA ranks,
- *       looks back and stores the previous tile.  Same memory traffic and
- *       workspace as the single pass.
+ *   BSHUFFLE_STRATEGY_PIPELINED  the single pass with its look-back taken
+ *       off the compute warps, for gathers and scatters of 4, 8 and 16-byte
+ *       elements and for indices (other calls run the plain single pass):
+ *       persistent CTAs; eight compute warps evaluate the bijection of a tile
+ *       and copy its kept elements into shared memory with cp.async, then
+ *       store the previous tile, which a ninth warp has meanwhile ranked
+ *       with the look-back.  Same memory traffic and workspace as the single
+ *       pass.
  *   BSHUFFLE_STRATEGY_AUTO (default)  staged when it applies and
- *       n * elem_bytes >= 256 MiB; otherwise the pipelined single pass for 4
- *       and 8-byte elements and the plain single pass for other widths; if
- *       the staged workspace cannot be allocated the single pass runs
- *       instead.
+ *       n * elem_bytes >= 256 MiB; otherwise the pipelined single pass,
+ *       except for gathers of 16-byte elements (plain single pass, faster
+ *       there); if the staged workspace cannot be allocated the single pass
+ *       runs instead.
  * The setting is process-wide.  Returns BSHUFFLE_ERR_INVALID for other values.
  */
 #define BSHUFFLE_STRATEGY_AUTO 0

@@ -223,15 +223,15 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     a.timeout_ns = g_timeout_ns.load();
     fill_keys(seed, rounds, a.keys);
     const bool rows = (mode == Mode::Gather || mode == Mode::Scatter) && elem_bytes > 16;
-    // the pipelined kernel: on request for 4, 8 and 16-byte elements, and by
-    // default for 4 and 8-byte elements (the plain kernel is faster for 16)
+    // the pipelined kernel: on request for every call it serves, and by
+    // default where it measured faster than the plain kernel (all but
+    // gathers of 16-byte elements)
     const int strategy = g_strategy.load();
-    const bool pipe_width = elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 16;
-    const bool pipe =
-        mode == Mode::Gather && pipe_width &&
-        (which == FusedKernel::Pipelined ||
-         (which == FusedKernel::ByStrategy &&
-          (strategy == BSHUFFLE_STRATEGY_PIPELINED || (strategy == BSHUFFLE_STRATEGY_AUTO && elem_bytes != 16))));
+    const bool auto_pipe = !(mode == Mode::Gather && elem_bytes == 16);
+    const bool pipe = !rows && bsh::pipe_supports(mode, elem_bytes) &&
+                      (which == FusedKernel::Pipelined ||
+                       (which == FusedKernel::ByStrategy &&
+                        (strategy == BSHUFFLE_STRATEGY_PIPELINED || (strategy == BSHUFFLE_STRATEGY_AUTO && auto_pipe))));
     const int config = rows ? 0 : bsh::elem_config_for(elem_bytes, mode, rounds);
     const uint64_t tile = rows ? bsh::rows_tile_size() : (pipe ? bsh::pipe_tile_size(elem_bytes) : bsh::elem_tile_size(config));
     const uint64_t tiles = (a.g.domain + tile - 1) / tile;
@@ -244,7 +244,7 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     cudaEvent_t *marks = mode == Mode::Gather ? timing_marks(ws) : nullptr;
     if (marks != nullptr && cudaEventRecord(marks[0], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
     const cudaError_t e = rows   ? bsh::launch_rows(a, mode, stream)
-                          : pipe ? bsh::launch_pipe(a, elem_bytes, stream)
+                          : pipe ? bsh::launch_pipe(a, mode, elem_bytes, stream)
                                  : bsh::launch_elem(a, mode, elem_bytes, config, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     if (marks != nullptr) {
@@ -294,7 +294,7 @@ int acquire_staged(cudaStream_t stream, Workspace *ws, size_t bytes)
 // single pass.  Returns BSHUFFLE_ERR_CUDA without launching anything if its
 // buffers cannot be allocated.
 int run_staged(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed, uint32_t rounds,
-               void *stream_ptr)
+               void *stream_ptr, bool inverse = false)
 {
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
     bsh::StagedArgs a{};
@@ -330,7 +330,7 @@ int run_staged(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint6
     cudaError_t e = cudaMemsetAsync(a.dst_cursor, 0, a.num_dst * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_fail(e);
     cudaEvent_t *marks = timing_marks(ws);
-    e = bsh::launch_staged(a, elem_bytes, stream, marks);
+    e = bsh::launch_staged(a, elem_bytes, inverse, stream, marks);
     if (e != cudaSuccess) return cuda_fail(e);
     ws->marks_recorded = marks != nullptr ? 3 : 0;
     return BSHUFFLE_OK;
@@ -397,6 +397,13 @@ int bshuffle_inverse(const void *in, void *out, uint64_t n, uint32_t elem_bytes,
     if (n == 0) return BSHUFFLE_OK;
     rc = check_buffers(in, out, n, elem_bytes);
     if (rc != BSHUFFLE_OK) return rc;
+    const int strategy = g_strategy.load();
+    if ((strategy == BSHUFFLE_STRATEGY_AUTO || strategy == BSHUFFLE_STRATEGY_STAGED) &&
+        staged_eligible(n, elem_bytes) && (strategy == BSHUFFLE_STRATEGY_STAGED || n * elem_bytes >= kStagedMinBytes)) {
+        rc = run_staged(in, out, n, elem_bytes, seed, rounds, stream, true);
+        if (rc == BSHUFFLE_OK || strategy == BSHUFFLE_STRATEGY_STAGED) return rc;
+        // auto: the staged buffers could not be had; the single pass needs none
+    }
     return run_fused(in, out, n, elem_bytes, seed, rounds, Mode::Scatter, stream);
 }
 

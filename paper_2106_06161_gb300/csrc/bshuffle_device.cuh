@@ -361,5 +361,80 @@ __device__ __forceinline__ void finish_launch(WsHeader *ws, uint32_t tag, uint32
     }
 }
 
+// ------------------------------------------------------------------ async copies and mbarriers
+// Helpers of the pipelined kernels: shared-memory mbarriers, cp.async copies
+// global -> shared, and a named barrier over a subset of the CTA's warps.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 state;\n\t"
+        "mbarrier.arrive.shared.b64 state, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+// Waits for the completion of the barrier phase of parity `parity`; gives up
+// (false) after `limit_ns` or when another role has raised `abort`.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                          const volatile uint32_t *abort)
+{
+    uint64_t start = 0;
+    uint32_t spins = 0;
+    while (!mbar_test(bar, parity)) {
+        if (*abort != 0u) return false;
+        const uint64_t now = global_ns();
+        if (start == 0) {
+            start = now;
+        } else if (now - start > limit_ns || ++spins > (1u << 26)) {
+            return false;
+        }
+    }
+    return true;
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src)
+{
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst_smem)), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Waits until every copy group of this thread but the most recent one has landed.
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Barrier 1 over the compute warps only.
+__device__ __forceinline__ void compute_sync(uint32_t threads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
+}
+
 }  // namespace dev
 }  // namespace bsh

@@ -149,10 +149,11 @@ struct StagedArgs {
 };
 
 uint32_t staged_tile_size();
-// Enqueue the two passes (elem_bytes 4, 8 or 16); the caller zeroes the
-// cursors first.  marks, when not null, are 3 events recorded before P1,
-// between the passes and after P2.
-cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, cudaStream_t stream,
+// Enqueue the two passes (elem_bytes 4, 8 or 16) of the shuffle, or of the
+// inverse shuffle when `inverse`; the caller zeroes the cursors first.
+// marks, when not null, are 3 events recorded before P1, between the passes
+// and after P2.
+cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, bool inverse, cudaStream_t stream,
                           cudaEvent_t *marks = nullptr);
 
 // ------------------------------------------------------------------ fusion ablation
@@ -203,9 +204,10 @@ struct McArgs {
 
 cudaError_t launch_mc(const McArgs &a, cudaStream_t stream);
 
-// Pipelined single pass (gather, 4/8/16-byte elements): tile size and launch.
+// Pipelined single pass: which calls it serves, its tile size, and launch.
+bool pipe_supports(Mode mode, uint32_t elem_bytes);
 uint32_t pipe_tile_size(uint32_t elem_bytes);
-cudaError_t launch_pipe(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream);
+cudaError_t launch_pipe(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream);
 
 struct ShapleyArgs {
     const uint32_t *w;  // player weights

@@ -174,9 +174,9 @@ struct BatchShared {
 // geometry, round keys) in buffer `nb`.  `prev` is the job of the CTA's
 // previous ticket (null before the first one); a CTA's tickets grow, so the
 // owner is `prev`'s instance or a later one.
-template <int ENTRIES>
+template <class SH>
 __device__ __forceinline__ void resolve_job(const BatchArgs &a, uint32_t ticket, uint64_t total,
-                                            const BatchJob *prev, BatchShared<ENTRIES> &sh, int nb)
+                                            const BatchJob *prev, SH &sh, int nb)
 {
     const uint32_t lane = threadIdx.x & 31u;
     BatchJob &job = sh.job[nb];
@@ -280,7 +280,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &a, const BatchJob &j
             }
         }
     }
-    if (warp == 1) resolve_job<ENTRIES>(a, __shfl_sync(kFull, next, 0), total, &sh.job[b], sh, b ^ 1);
+    if (warp == 1) resolve_job(a, __shfl_sync(kFull, next, 0), total, &sh.job[b], sh, b ^ 1);
     __syncthreads();
 }
 
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kBBlock, min_ctas_for(sizeof(T))) batch_tile_k
     if (warp == 1) {
         uint32_t t0 = 0;
         if ((threadIdx.x & 31u) == 0) t0 = atomicAdd(&a.ws->batch_ticket, 1u);
-        resolve_job<ENTRIES>(a, __shfl_sync(kFull, t0, 0), total, nullptr, sh, 0);
+        resolve_job(a, __shfl_sync(kFull, t0, 0), total, nullptr, sh, 0);
     }
     __syncthreads();
     for (int b = 0;; b ^= 1) {
@@ -320,6 +320,241 @@ __global__ void __launch_bounds__(kBBlock, min_ctas_for(sizeof(T))) batch_tile_k
             __threadfence();
         }
     }
+}
+
+// ------------------------------------------------------------------ pipelined
+// The batched shuffle with the look-back taken off the compute warps (the
+// schedule of kernels_pipe.cu): eight compute warps evaluate the bijection of
+// tile i, copy its kept elements into a shared buffer with cp.async and
+// publish its aggregate, then store tile i - 1 once a ninth warp has ranked
+// it (look-back bounded by the instance's first tile).  After its stores,
+// warp 0 takes the next ticket and resolves its instance.  Tickets are taken
+// only when the CTA no longer waits on other tiles, and aggregates never wait
+// on a look-back.  Used for 4- and 8-byte elements.
+constexpr int kPipeWarps = 8;
+constexpr int kPipeItems = kTile / (kPipeWarps * 32);
+static_assert(kPipeItems * kPipeWarps * 32 == static_cast<int>(kTile), "tile shape");
+
+struct BatchPipeShared {
+    static constexpr int E = kPipeWarps * kPipeItems;
+    uint64_t full[2];            // compute -> look-back: ballots of the buffer's tile written
+    uint64_t ranked[2];          // look-back -> compute: offsets and prefix ready
+    unsigned long long aggc[2];  // (compute warps done << 32) | kept count
+    BatchJob job[2];
+    uint32_t keys[2][kMaxRounds];
+    uint32_t masks[2][E];
+    uint32_t offs[2][E];
+    uint32_t prefix[2];
+    uint32_t ok[2];
+    uint32_t abort;
+};
+
+template <class T>
+__global__ void __launch_bounds__((kPipeWarps + 1) * 32, 3) batch_pipe_kernel(const __grid_constant__ BatchArgs a)
+{
+    constexpr uint32_t NCT = kPipeWarps * 32;
+    constexpr int E = BatchPipeShared::E;
+    __shared__ BatchPipeShared sh;
+    extern __shared__ __align__(16) unsigned char batch_dyn[];
+    T *vals = reinterpret_cast<T *>(batch_dyn);  // [2][kTile]
+    const dev::StatusRing ring{a.status, kRingWords - 1, kRingShift, 1u};
+    const uint64_t total = *reinterpret_cast<volatile const uint64_t *>(a.total_tiles);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint64_t role_limit = 2 * a.timeout_ns + 1000000000ull;
+    volatile uint32_t *abort = &sh.abort;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            dev::mbar_init(&sh.full[b], kPipeWarps);
+            dev::mbar_init(&sh.ranked[b], 1);
+            sh.aggc[b] = 0ull;
+        }
+        sh.abort = 0u;
+    }
+    if (warp == 0) {
+        uint32_t t0 = 0;
+        if (lane == 0) t0 = atomicAdd(&a.ws->batch_ticket, 1u);
+        resolve_job(a, __shfl_sync(kFull, t0, 0), total, nullptr, sh, 0);
+    }
+    __syncthreads();
+
+    if (warp < kPipeWarps) {
+        // ---------------------------------------------------------- compute
+        const uint32_t ct = threadIdx.x;
+        const uint32_t lt = dev::lanemask_lt();
+        T *prev_out = nullptr;  // the previous tile's output and length
+        uint32_t prev_n = 0;
+        for (uint32_t iter = 0;; ++iter) {
+            const int b = static_cast<int>(iter & 1u);
+            const int pb = b ^ 1;
+            const BatchJob job = sh.job[b];
+            const uint32_t tile = job.ticket;
+            const bool stop = tile >= total;
+            if (!stop) {
+                const Geometry &g = job.g;
+                const uint32_t base = (tile - static_cast<uint32_t>(job.first)) * kTile;
+                uint32_t left[kPipeItems], right[kPipeItems];
+#pragma unroll
+                for (int j = 0; j < kPipeItems; ++j) {
+                    const uint32_t i = base + static_cast<uint32_t>(j) * NCT + ct;
+                    left[j] = i >> g.R;
+                    right[j] = i & g.rmask;
+                }
+                if (g.k & 1u)
+                    dev::cipher_items<true, kPipeItems>(left, right, sh.keys[b], a.rounds, g);
+                else
+                    dev::cipher_items<false, kPipeItems>(left, right, sh.keys[b], a.rounds, g);
+                const T *in = static_cast<const T *>(job.in);
+                T *buf = vals + static_cast<size_t>(b) * kTile;
+                uint32_t count = 0;
+#pragma unroll
+                for (int j = 0; j < kPipeItems; ++j) {
+                    const uint32_t i = base + static_cast<uint32_t>(j) * NCT + ct;
+                    const uint32_t src = (left[j] << g.R) | right[j];
+                    const bool keep = static_cast<uint64_t>(i) < g.domain && src < g.n;
+                    if (keep) dev::cp_async<sizeof(T)>(buf + static_cast<uint32_t>(j) * NCT + ct, in + src);
+                    const uint32_t m = __ballot_sync(kFull, keep);
+                    count += __popc(m);
+                    if (lane == 0) sh.masks[b][j * kPipeWarps + warp] = m;
+                }
+                if (lane == 0) {
+                    const unsigned long long v = atomicAdd(&sh.aggc[b], (1ull << 32) | count);
+                    if ((v >> 32) == kPipeWarps - 1 && static_cast<int64_t>(tile) != a.skip_publish_tile) {
+                        const uint32_t sum = static_cast<uint32_t>(v) + count;
+                        dev::st_relaxed_gpu(ring.slot(tile), dev::status_word(ring.tag(tile), tile == job.first, sum));
+                    }
+                }
+            }
+            dev::cp_async_commit();
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&sh.full[b]);
+            uint32_t next = 0xffffffffu;
+            if (iter > 0) {
+                const bool ranked = dev::mbar_wait(&sh.ranked[pb], ((iter - 1u) >> 1) & 1u, role_limit, abort);
+                if (!ranked) {
+                    if (lane == 0) dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
+                    *abort = 1u;
+                }
+                // the previous tile's look-back is over: take the next ticket now
+                if (ct == 0 && !stop && *abort == 0u) next = atomicAdd(&a.ws->batch_ticket, 1u);
+                dev::cp_async_wait_prior();
+                if (ranked && sh.ok[pb] != 0u) {
+                    const T *pbuf = vals + static_cast<size_t>(pb) * kTile;
+                    const uint32_t prefix = sh.prefix[pb];
+#pragma unroll
+                    for (int j = 0; j < kPipeItems; ++j) {
+                        const uint32_t e = static_cast<uint32_t>(j) * kPipeWarps + warp;
+                        const uint32_t m = sh.masks[pb][e];
+                        if ((m >> lane) & 1u) {
+                            const uint32_t dst = prefix + sh.offs[pb][e] + __popc(m & lt);
+                            if (dst < prev_n) prev_out[dst] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
+                            else dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
+                        }
+                    }
+                }
+            } else if (ct == 0 && !stop) {
+                next = atomicAdd(&a.ws->batch_ticket, 1u);
+            }
+            if (stop) break;
+            prev_out = static_cast<T *>(job.out);
+            prev_n = job.g.n;
+            if (warp == 0) resolve_job(a, __shfl_sync(kFull, next, 0), total, &sh.job[b], sh, pb);
+            dev::compute_sync(NCT);
+        }
+        dev::cp_async_wait_all();
+    } else {
+        // -------------------------------------------------------- look-back
+        for (uint32_t iter = 0;; ++iter) {
+            const int b = static_cast<int>(iter & 1u);
+            const uint32_t parity = (iter >> 1) & 1u;
+            bool full = false;
+            if (lane == 0) {
+                full = dev::mbar_wait(&sh.full[b], parity, role_limit, abort);
+                if (!full) {
+                    dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
+                    *abort = 1u;
+                }
+            }
+            if (!__shfl_sync(kFull, full, 0)) break;
+            (void)dev::mbar_test(&sh.full[b], parity);  // completed phase: every lane acquires it
+            const uint32_t tile = sh.job[b].ticket;
+            if (tile >= total) break;
+            const uint64_t first = sh.job[b].first;
+            constexpr int C = (E + 31) / 32;
+            uint32_t local[C];
+            uint32_t sum = 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int e = static_cast<int>(lane) * C + c;
+                local[c] = e < E ? static_cast<uint32_t>(__popc(sh.masks[b][e])) : 0u;
+                sum += local[c];
+            }
+            const uint32_t incl = dev::warp_inclusive_scan(sum);
+            uint32_t run = incl - sum;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int e = static_cast<int>(lane) * C + c;
+                if (e < E) sh.offs[b][e] = run;
+                run += local[c];
+            }
+            const uint32_t aggregate = __shfl_sync(kFull, incl, 31);
+            uint32_t prefix = 0;
+            bool ok = true;
+            if (tile > first) {
+                prefix = dev::lookback(ring, tile, first, a.timeout_ns, ok);
+                if (lane == 0 && static_cast<int64_t>(tile) != a.skip_publish_tile)
+                    dev::st_relaxed_gpu(ring.slot(tile), dev::status_word(ring.tag(tile), true, prefix + aggregate));
+                if (lane == 0 && !ok) dev::record_error(a.ws, dev::kErrLookbackTimeout, tile);
+            }
+            if (lane == 0) {
+                sh.prefix[b] = prefix;
+                sh.ok[b] = ok ? 1u : 0u;
+                sh.aggc[b] = 0ull;
+            }
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&sh.ranked[b]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t d = atomicAdd(&a.ws->batch_done, 1u);
+        if (d == gridDim.x - 1u) {
+            atomicExch(&a.ws->batch_ticket, 0u);
+            atomicExch(&a.ws->batch_done, 0u);
+            __threadfence();
+        }
+    }
+}
+
+template <class T>
+cudaError_t launch_pipe_typed(const BatchArgs &a, cudaStream_t stream)
+{
+    constexpr int THREADS = (kPipeWarps + 1) * 32;
+    constexpr size_t DYN = 2 * sizeof(T) * kTile;
+    static int per_sm[64] = {0};
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (per_sm[device] == 0) {
+        e = cudaFuncSetAttribute(batch_pipe_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(DYN));
+        if (e != cudaSuccess) return e;
+        int blocks = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_pipe_kernel<T>, THREADS, DYN);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return e;
+        per_sm[device] = (blocks > 0 ? blocks : 1) * sms;
+    }
+    BatchArgs b = a;
+    b.grid = static_cast<uint32_t>(per_sm[device]);
+    batch_plan_kernel<<<1, kPlanThreads, 0, stream>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_pipe_kernel<T><<<b.grid, THREADS, DYN, stream>>>(b);
+    return cudaGetLastError();
 }
 
 template <class T>
@@ -357,9 +592,9 @@ cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream)
     switch (a.elem_bytes) {
     case 1: return launch_typed<unsigned char>(a, stream);
     case 2: return launch_typed<unsigned short>(a, stream);
-    case 4: return launch_typed<unsigned int>(a, stream);
-    case 8: return launch_typed<unsigned long long>(a, stream);
-    case 16: return launch_typed<uint4>(a, stream);
+    case 4: return launch_pipe_typed<unsigned int>(a, stream);
+    case 8: return launch_pipe_typed<unsigned long long>(a, stream);
+    case 16: return launch_typed<uint4>(a, stream);  // the plain kernel measured faster here
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,6 +1,6 @@
-// Pipelined single pass of Algorithm 1 (gather mode, 4-, 8- and 16-byte
-// elements): the same output as the fused tile kernel, with the inter-tile
-// look-back taken off the compute warps' path.
+// Pipelined single pass of Algorithm 1 (gather and scatter of 4-, 8- and
+// 16-byte elements, and the index output): the same output as the fused tile
+// kernel, with the inter-tile look-back taken off the compute warps' path.
 //
 // In the plain fused kernel every warp of a tile waits while one warp looks
 // back, and under a full load of random gathers a look-back takes several
@@ -24,6 +24,7 @@
 // smallest unfinished ticket therefore always makes progress.  Every wait is
 // bounded.
 #include <cstdint>
+#include <type_traits>
 
 #include "bshuffle_device.cuh"
 #include "bshuffle_internal.h"
@@ -48,77 +49,6 @@ constexpr int kPipeComputeWarps = 8;
 constexpr int pipe_items(uint32_t elem_bytes) { return elem_bytes >= 16 ? BSHUFFLE_PIPE_ITEMS16 : 8; }
 constexpr uint32_t pipe_tile(uint32_t elem_bytes) { return kPipeComputeWarps * 32 * pipe_items(elem_bytes); }
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile(
-        "{\n\t.reg .b64 state;\n\t"
-        "mbarrier.arrive.shared.b64 state, [%0];\n\t}" ::"r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0u;
-}
-
-// Waits for the completion of the barrier phase of parity `parity`; gives up
-// (false) after `limit_ns` or when another role has raised `abort`.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
-                                          const volatile uint32_t *abort)
-{
-    uint64_t start = 0;
-    uint32_t spins = 0;
-    while (!mbar_test(bar, parity)) {
-        if (*abort != 0u) return false;
-        const uint64_t now = dev::global_ns();
-        if (start == 0) {
-            start = now;
-        } else if (now - start > limit_ns || ++spins > (1u << 26)) {
-            return false;
-        }
-    }
-    return true;
-}
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *dst_smem, const void *src)
-{
-    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst_smem)), "l"(src), "n"(BYTES)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// Waits until every copy group of this thread but the most recent one has landed.
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// Barrier 1 over the compute warps only.
-__device__ __forceinline__ void compute_sync(uint32_t threads)
-{
-    asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
-}
-
 template <int NCW, int ITEMS>
 struct PipeShared {
     static constexpr int E = NCW * ITEMS;
@@ -134,15 +64,22 @@ struct PipeShared {
     uint32_t abort;
 };
 
-template <class T, bool ODD, int NCW, int ITEMS>
+// What a tile buffer holds per domain index: the gathered element (gather),
+// the image itself (indices), or the image as a 32-bit target slot (scatter:
+// out[f(i_j)] = in[j] reads its element once the tile's ranks are known).
+template <class T, Mode MODE>
+using PipeSlot = typename std::conditional<MODE == Mode::Scatter, uint32_t, T>::type;
+
+template <class T, Mode MODE, bool ODD, int NCW, int ITEMS>
 __global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_tile_kernel(const __grid_constant__ TileArgs a)
 {
+    using S = PipeSlot<T, MODE>;
     constexpr uint32_t NCT = NCW * 32;  // compute threads
     constexpr uint32_t TILE = NCT * ITEMS;
     constexpr int E = NCW * ITEMS;
     __shared__ PipeShared<NCW, ITEMS> sh;
     extern __shared__ __align__(16) unsigned char pipe_dyn[];
-    T *vals = reinterpret_cast<T *>(pipe_dyn);  // [2][TILE], natural (item, thread) order
+    S *vals = reinterpret_cast<S *>(pipe_dyn);  // [2][TILE], natural (item, thread) order
 
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
@@ -151,8 +88,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_t
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&sh.full[b], NCW);
-            mbar_init(&sh.ranked[b], 1);
+            dev::mbar_init(&sh.full[b], NCW);
+            dev::mbar_init(&sh.ranked[b], 1);
             sh.aggc[b] = 0ull;
         }
         sh.tag = dev::ld_relaxed_gpu(&a.ws->tag);
@@ -172,7 +109,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_t
         for (uint32_t iter = 0;; ++iter) {
             const int b = static_cast<int>(iter & 1u);
             if (ct == 0) sh.ticket[b] = *abort == 0u ? atomicAdd(&a.ws->ticket, 1u) : 0xffffffffu;
-            compute_sync(NCT);
+            dev::compute_sync(NCT);
             const uint32_t tile = sh.ticket[b];
             const bool stop = tile >= a.num_tiles;
             if (!stop) {
@@ -185,14 +122,20 @@ __global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_t
                     right[j] = i & a.g.rmask;
                 }
                 dev::cipher_items<ODD, ITEMS>(left, right, a.keys, a.rounds, a.g);
-                T *buf = vals + static_cast<size_t>(b) * TILE;
+                S *buf = vals + static_cast<size_t>(b) * TILE;
                 uint32_t count = 0;
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) {
                     const uint32_t i = base + static_cast<uint32_t>(j) * NCT + ct;
                     const uint32_t src = (left[j] << a.g.R) | right[j];
                     const bool keep = static_cast<uint64_t>(i) < a.g.domain && src < a.g.n;
-                    if (keep) cp_async<sizeof(T)>(buf + static_cast<uint32_t>(j) * NCT + ct, in + src);
+                    if (keep) {
+                        S *slot = buf + static_cast<uint32_t>(j) * NCT + ct;
+                        if constexpr (MODE == Mode::Gather)
+                            dev::cp_async<sizeof(T)>(slot, in + src);
+                        else
+                            *slot = static_cast<S>(src);
+                    }
                     const uint32_t m = __ballot_sync(kFull, keep);
                     count += __popc(m);
                     if (lane == 0) sh.masks[b][j * NCW + warp] = m;
@@ -205,36 +148,60 @@ __global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_t
                     }
                 }
             }
-            cp_async_commit();
+            dev::cp_async_commit();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.full[b]);
+            if (lane == 0) dev::mbar_arrive(&sh.full[b]);
             if (iter > 0) {
                 // store the previous tile (buffer b ^ 1) once it is ranked
                 const int pb = b ^ 1;
-                const bool ranked = mbar_wait(&sh.ranked[pb], ((iter - 1u) >> 1) & 1u, role_limit, abort);
+                const bool ranked = dev::mbar_wait(&sh.ranked[pb], ((iter - 1u) >> 1) & 1u, role_limit, abort);
                 if (!ranked) {
                     if (lane == 0) dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
                     *abort = 1u;
                 }
-                cp_async_wait_prior();  // this thread's copies of the previous tile have landed
+                dev::cp_async_wait_prior();  // this thread's copies of the previous tile have landed
                 if (ranked && sh.ok[pb] != 0u) {
-                    const T *pbuf = vals + static_cast<size_t>(pb) * TILE;
+                    const S *pbuf = vals + static_cast<size_t>(pb) * TILE;
                     const uint32_t prefix = sh.prefix[pb];
+                    if constexpr (MODE == Mode::Scatter) {
+                        // coalesced reads of this tile's slots, then the random writes
+                        uint32_t target[ITEMS];
+                        T val[ITEMS];
 #pragma unroll
-                    for (int j = 0; j < ITEMS; ++j) {
-                        const uint32_t e = static_cast<uint32_t>(j) * NCW + warp;
-                        const uint32_t m = sh.masks[pb][e];
-                        if ((m >> lane) & 1u) {
-                            const uint32_t dst = prefix + sh.offs[pb][e] + __popc(m & lt);
-                            if (dst < a.g.n) out[dst] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
-                            else dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
+                        for (int j = 0; j < ITEMS; ++j) {
+                            const uint32_t e = static_cast<uint32_t>(j) * NCW + warp;
+                            const uint32_t m = sh.masks[pb][e];
+                            target[j] = 0xffffffffu;
+                            if ((m >> lane) & 1u) {
+                                const uint32_t dst = prefix + sh.offs[pb][e] + __popc(m & lt);
+                                if (dst < a.g.n) {
+                                    target[j] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
+                                    val[j] = __ldg(in + dst);
+                                } else {
+                                    dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < ITEMS; ++j)
+                            if (target[j] < a.g.n) out[target[j]] = val[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < ITEMS; ++j) {
+                            const uint32_t e = static_cast<uint32_t>(j) * NCW + warp;
+                            const uint32_t m = sh.masks[pb][e];
+                            if ((m >> lane) & 1u) {
+                                const uint32_t dst = prefix + sh.offs[pb][e] + __popc(m & lt);
+                                if (dst < a.g.n) out[dst] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
+                                else dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
+                            }
                         }
                     }
                 }
             }
             if (stop) break;
         }
-        cp_async_wait_all();
+        dev::cp_async_wait_all();
     } else {
         // -------------------------------------------------------- look-back
         for (uint32_t iter = 0;; ++iter) {
@@ -243,14 +210,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_t
             // lane 0 waits, so that the warp leaves the loop as one
             bool full = false;
             if (lane == 0) {
-                full = mbar_wait(&sh.full[b], parity, role_limit, abort);
+                full = dev::mbar_wait(&sh.full[b], parity, role_limit, abort);
                 if (!full) {
                     dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
                     *abort = 1u;
                 }
             }
             if (!__shfl_sync(kFull, full, 0)) break;
-            (void)mbar_test(&sh.full[b], parity);  // completed phase: every lane acquires it
+            (void)dev::mbar_test(&sh.full[b], parity);  // completed phase: every lane acquires it
             const uint32_t tile = sh.ticket[b];
             if (tile >= a.num_tiles) break;
             constexpr int C = (E + 31) / 32;
@@ -285,26 +252,26 @@ __global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_t
                 sh.aggc[b] = 0ull;
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.ranked[b]);
+            if (lane == 0) dev::mbar_arrive(&sh.ranked[b]);
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) dev::finish_launch(a.ws, tag, gridDim.x);
 }
 
-template <class T>
+template <class T, Mode MODE>
 cudaError_t launch_typed(const TileArgs &a, cudaStream_t stream)
 {
     constexpr int NCW = kPipeComputeWarps, ITEMS = pipe_items(sizeof(T));
     constexpr int THREADS = (NCW + 1) * 32;
-    constexpr size_t DYN = sizeof(T) * 2 * pipe_tile(sizeof(T));
+    constexpr size_t DYN = sizeof(PipeSlot<T, MODE>) * 2 * pipe_tile(sizeof(T));
     static int per_sm[64][2] = {};
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     const bool odd = (a.g.k & 1u) != 0u;
-    auto kernel = odd ? pipe_tile_kernel<T, true, NCW, ITEMS> : pipe_tile_kernel<T, false, NCW, ITEMS>;
+    auto kernel = odd ? pipe_tile_kernel<T, MODE, true, NCW, ITEMS> : pipe_tile_kernel<T, MODE, false, NCW, ITEMS>;
     int &ctas = per_sm[device][odd ? 1 : 0];
     if (ctas == 0) {
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(DYN));
@@ -325,14 +292,38 @@ cudaError_t launch_typed(const TileArgs &a, cudaStream_t stream)
 
 uint32_t pipe_tile_size(uint32_t elem_bytes) { return pipe_tile(elem_bytes); }
 
-cudaError_t launch_pipe(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream)
+bool pipe_supports(Mode mode, uint32_t elem_bytes)
 {
-    switch (elem_bytes) {
-    case 4: return launch_typed<unsigned int>(a, stream);
-    case 8: return launch_typed<unsigned long long>(a, stream);
-    case 16: return launch_typed<uint4>(a, stream);
-    default: return cudaErrorInvalidValue;
+    switch (mode) {
+    case Mode::Gather:
+    case Mode::Scatter: return elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 16;
+    case Mode::Index32:
+    case Mode::Index64: return true;
     }
+    return false;
+}
+
+cudaError_t launch_pipe(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream)
+{
+    switch (mode) {
+    case Mode::Index32: return launch_typed<unsigned int, Mode::Index32>(a, stream);
+    case Mode::Index64: return launch_typed<unsigned long long, Mode::Index64>(a, stream);
+    case Mode::Gather:
+        switch (elem_bytes) {
+        case 4: return launch_typed<unsigned int, Mode::Gather>(a, stream);
+        case 8: return launch_typed<unsigned long long, Mode::Gather>(a, stream);
+        case 16: return launch_typed<uint4, Mode::Gather>(a, stream);
+        default: return cudaErrorInvalidValue;
+        }
+    case Mode::Scatter:
+        switch (elem_bytes) {
+        case 4: return launch_typed<unsigned int, Mode::Scatter>(a, stream);
+        case 8: return launch_typed<unsigned long long, Mode::Scatter>(a, stream);
+        case 16: return launch_typed<uint4, Mode::Scatter>(a, stream);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace bsh

@@ -1,6 +1,8 @@
 // Staged shuffle of power-of-two lengths much larger than L2: the same
 // permutation as the fused single pass (Algorithm 1, Sec. 4), with every HBM
 // access sequential and the random accesses confined to L2-resident windows.
+// The inverse shuffle (out[f(j)] = in[j]) runs the same two passes with the
+// forward cipher in place of the inverse one.
 //
 // On GB300 a random 8-byte access to a multi-GiB array is bound by the HBM
 // random-access rate (~47 G accesses/s), far below the streaming bandwidth, so
@@ -65,7 +67,9 @@ __device__ __forceinline__ void block_exclusive_scan(const uint32_t *cnt, uint32
 // Streaming read of data used once (evict-first in L1 and L2).
 // ------------------------------------------------------------------ P1
 
-template <class T, bool ODD>
+// FORWARD: element b goes to slot f(b) (the inverse shuffle) instead of
+// f^-1(b) (the shuffle).
+template <class T, bool ODD, bool FORWARD>
 __global__ void __launch_bounds__(kSBlock) staged_bucket_kernel(const __grid_constant__ StagedArgs a)
 {
     extern __shared__ uint32_t s_dyn[];  // 3 * num_dst words
@@ -92,11 +96,14 @@ __global__ void __launch_bounds__(kSBlock) staged_bucket_kernel(const __grid_con
         left[j] = b >> g.R;
         right[j] = b & g.rmask;
     }
-    dev::cipher_inverse_items<ODD, kSItems>(left, right, a.keys, a.rounds, g);
+    if constexpr (FORWARD)
+        dev::cipher_items<ODD, kSItems>(left, right, a.keys, a.rounds, g);
+    else
+        dev::cipher_inverse_items<ODD, kSItems>(left, right, a.keys, a.rounds, g);
     uint32_t bucket[kSItems], pos[kSItems], slot[kSItems];
 #pragma unroll
     for (int j = 0; j < kSItems; ++j) {
-        const uint32_t dst = (left[j] << g.R) | right[j];  // f^-1(b): the element's output slot
+        const uint32_t dst = (left[j] << g.R) | right[j];  // f^-1(b) (or f(b)): the element's output slot
         bucket[j] = dst >> a.dst_shift;
         pos[j] = dst & ((1u << a.dst_shift) - 1u);
     }
@@ -170,7 +177,7 @@ cudaError_t mark(cudaEvent_t *marks, int i, cudaStream_t stream)
     return marks != nullptr ? cudaEventRecord(marks[i], stream) : cudaSuccess;
 }
 
-template <class T>
+template <class T, bool FORWARD>
 cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *marks)
 {
     static bool configured[64] = {false};
@@ -179,11 +186,11 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     if (!configured[device]) {
-        e = cudaFuncSetAttribute(staged_bucket_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(staged_bucket_kernel<T, true, FORWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  3 * 4096 * 4);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(staged_bucket_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     3 * 4096 * 4);
+            e = cudaFuncSetAttribute(staged_bucket_kernel<T, false, FORWARD>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 4);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(staged_scatter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(kScatterSmemReserve));
@@ -195,9 +202,9 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
     e = mark(marks, 0, stream);
     if (e != cudaSuccess) return e;
     if (a.g.k & 1u)
-        staged_bucket_kernel<T, true><<<chunks, kSBlock, dyn, stream>>>(a);
+        staged_bucket_kernel<T, true, FORWARD><<<chunks, kSBlock, dyn, stream>>>(a);
     else
-        staged_bucket_kernel<T, false><<<chunks, kSBlock, dyn, stream>>>(a);
+        staged_bucket_kernel<T, false, FORWARD><<<chunks, kSBlock, dyn, stream>>>(a);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = mark(marks, 1, stream);
     if (e != cudaSuccess) return e;
@@ -211,15 +218,18 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
 
 uint32_t staged_tile_size() { return kSTile; }
 
-cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, cudaStream_t stream, cudaEvent_t *marks)
+cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, bool inverse, cudaStream_t stream,
+                          cudaEvent_t *marks)
 {
     if (a.num_dst > 4096 || static_cast<uint64_t>(a.g.n) != a.g.domain || a.g.domain < 2 * kSTile ||
         a.g.domain > (uint64_t{1} << 31) || (uint64_t{1} << a.dst_shift) < kSTile)
         return cudaErrorInvalidValue;
     switch (elem_bytes) {
-    case 4: return launch_typed<unsigned int>(a, stream, marks);
-    case 8: return launch_typed<unsigned long long>(a, stream, marks);
-    case 16: return launch_typed<uint4>(a, stream, marks);
+    case 4: return inverse ? launch_typed<unsigned int, true>(a, stream, marks)
+                           : launch_typed<unsigned int, false>(a, stream, marks);
+    case 8: return inverse ? launch_typed<unsigned long long, true>(a, stream, marks)
+                           : launch_typed<unsigned long long, false>(a, stream, marks);
+    case 16: return inverse ? launch_typed<uint4, true>(a, stream, marks) : launch_typed<uint4, false>(a, stream, marks);
     default: return cudaErrorInvalidValue;
     }
 }

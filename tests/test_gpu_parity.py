@@ -160,11 +160,17 @@ def test_full_size_power_of_two_u64_sampled():
     assert torch.equal(torch.sort(y).values, torch.sort(xd).values)
 
 
-def test_full_size_worst_case_padding_exact():
+@pytest.fixture(scope="module")
+def worst_case_indices():
+    # one oracle pass of the n = 2^28 + 12345 shuffle with seed 0
+    return oracle.indices(2**28 + 12345, 0)
+
+
+def test_full_size_worst_case_padding_exact(worst_case_indices):
     # n = 2^28 + 12345 (domain 2^29, about half the images dropped): one full
     # oracle pass, compared slot for slot with the GPU's indices and payload.
     n, seed = 2**28 + 12345, 0
-    want = oracle.indices(n, seed)
+    want = worst_case_indices
     idx = bs.indices(n, seed, dtype=torch.int64)
     assert_no_device_error()
     assert np.array_equal(idx.cpu().numpy().view(np.uint64), want)
@@ -175,6 +181,26 @@ def test_full_size_worst_case_padding_exact():
     js = np.concatenate([np.arange(2048), rng.integers(0, n, 300_000), np.arange(n - 2048, n)])
     got = y[torch.from_numpy(js).cuda()].cpu().numpy().view(np.uint64)
     assert np.array_equal(got, x[want[js].astype(np.int64)])
+
+
+@pytest.mark.parametrize("width", [4, 16])
+def test_full_size_other_widths_sampled(width, worst_case_indices):
+    # the sweep's largest sizes for 4- and 16-byte elements through the
+    # default strategy (staged at 2^28, a single pass at 2^28 + 12345)
+    rng = np.random.default_rng(width)
+    for n in (2**28, 2**28 + 12345):
+        x = workloads.sweep_payload(n, width, 0)
+        y = bs.permute(to_device(x), 0)
+        assert_no_device_error()
+        js = np.concatenate([np.arange(2048), rng.integers(0, n, 200_000), np.arange(n - 2048, n)])
+        if n == 2**28:
+            src = oracle.varphilox(js.astype(np.uint64), 28, oracle.round_keys(0, 24)).astype(np.int64)
+        else:
+            src = worst_case_indices[js].astype(np.int64)
+        got = y[torch.from_numpy(js).cuda()].cpu().numpy()
+        want = x[src]
+        assert np.array_equal(got.view(np.uint8).reshape(len(js), -1), want.view(np.uint8).reshape(len(js), -1)), n
+        del y
 
 
 def test_full_size_other_seeds_properties():

@@ -1,7 +1,8 @@
 """The pipelined single pass (BSHUFFLE_STRATEGY_PIPELINED) against the
-oracle: the same output as Algorithm 1, bit for bit, for 4-, 8- and 16-byte
-elements, small sizes with ragged last tiles up to the full worst-case
-length, plus its bounded waits and the widths it hands to the plain kernel."""
+oracle: the same output as Algorithm 1, bit for bit, for gathers and
+scatters of 4-, 8- and 16-byte elements and for the index output, small
+sizes with ragged last tiles up to the full worst-case length, plus its
+bounded waits and the widths it hands to the plain kernel."""
 import numpy as np
 import pytest
 import torch
@@ -53,6 +54,28 @@ def test_rounds(bs, rounds):
         assert np.array_equal(_gpu(bs, x, 5, rounds), oracle.permute(x, 5, rounds))
 
 
+@pytest.mark.parametrize("idx_dtype", [torch.int32, torch.int64])
+def test_indices_match_oracle(bs, idx_dtype):
+    for n in (1, 3, 2047, 2049, 70_001, 1_000_003):
+        for seed in (0, 4):
+            got = bs.indices(n, seed, dtype=idx_dtype)
+            assert_no_device_error()
+            want = oracle.indices(n, seed)
+            assert np.array_equal(got.cpu().numpy().astype(np.uint64), want), (n, seed)
+
+
+@pytest.mark.parametrize("width", [1, 4, 8, 16])
+def test_inverse_matches_oracle(bs, width):
+    for n in (1, 5, 2049, 65537, 300_007):
+        x = _payload(n, width, 3)
+        y = bs.inverse(to_device(x), 8)
+        assert_no_device_error()
+        assert np.array_equal(to_host(y, x), oracle.inverse(x, 8)), n
+        # inverse undoes permute
+        z = bs.inverse(bs.permute(to_device(x), 8), 8)
+        assert np.array_equal(to_host(z, x), x), n
+
+
 def test_other_widths_use_the_plain_kernel(bs):
     for width in (1, 2, 32):
         x = _payload(10_007, width, 1)
@@ -69,6 +92,10 @@ def test_many_tiles_per_cta(bs):
 def test_full_size_worst_case_sampled(bs):
     n, seed = 2**28 + 12345, 0
     want = oracle.indices(n, seed)
+    idx = bs.indices(n, seed, dtype=torch.int64)
+    assert_no_device_error()
+    assert np.array_equal(idx.cpu().numpy().view(np.uint64), want)
+    del idx
     x = workloads.uniform_u64(n, seed)
     y = bs.permute(to_device(x), seed)
     assert_no_device_error()
