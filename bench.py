@@ -477,6 +477,20 @@ def secondary(bs, torch, dev, stream):
         bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
         del x, y
 
+    # the inverse shuffle (staged with the forward cipher at 2^28, the
+    # pipelined single pass at 2^28 + 12345) and the index output
+    for label, n_ in (("2p28", N_MAIN), ("2p28_plus_12345", N_WORST)):
+        x = torch.empty(n_, dtype=torch.int64, device=dev).random_()
+        y = torch.empty_like(x)
+        inv = lambda: bs.bshuffle_inverse(x.data_ptr(), y.data_ptr(), n_, ELEM, 5, ROUNDS, sptr)  # noqa: E731
+        idx = lambda: bs.bshuffle_indices(y.data_ptr(), 8, n_, 5, ROUNDS, sptr)  # noqa: E731
+        for fn, name in ((inv, "inverse"), (idx, "indices64")):
+            for _ in range(3):
+                fn()
+            per, region = timed_launches(fn, 10, stream, torch)
+            out[f"{name}_{label}_u64"] = {"ms": region / 10, "elements_per_s": n_ * 10 / (region * 1e-3)}
+        del x, y
+
     # the fusion experiment of Sec. 6 at worst-case padding: Bijective0
     # (separate passes), Bijective1 (two-pass scan), Bijective2 (single pass)
     for w in (20, 24, 28):
