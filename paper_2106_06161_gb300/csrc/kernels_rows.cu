@@ -2,11 +2,15 @@
 // multiple of 16 and larger than 16: Algorithm 1 of Sec. 4 with each X[b]
 // being a whole row.
 //
-// A CTA owns ROWS_PER_TILE consecutive domain indices, one per thread.  It
-// evaluates the bijection, ranks the kept indices, looks back for the tile's
-// global prefix, records the (source, slot) pairs in shared memory, and then
-// every warp copies whole rows with 16-byte vector loads and stores: rows are
-// contiguous, so both sides of the copy are fully coalesced.
+// A CTA owns kRowsPerTile consecutive domain indices, one per thread of its
+// first warps.  It evaluates the bijection, ranks the kept indices, looks back
+// for the tile's global prefix, records the (source, slot) pairs in shared
+// memory, and then all its warps copy whole rows with 16-byte vector loads
+// and stores: rows are contiguous, so both sides of the copy are fully
+// coalesced.  Tiles are small and each lane keeps up to 8 loads in flight
+// (a 4 KiB row per warp step), so that enough bytes are in flight per SM to
+// cover the HBM latency: with 256 rows per tile a [65536 x 1024] FP32
+// shuffle had fewer than two CTAs per SM and was latency-bound.
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -18,14 +22,17 @@ namespace {
 using dev::kFull;
 
 constexpr int kRowBlock = 256;
+constexpr int kRowsPerTile = 64;
+constexpr int kRowChunkUnroll = 8;
 
 template <Mode MODE, bool ODD>
 __global__ void __launch_bounds__(kRowBlock) rows_tile_kernel(const __grid_constant__ TileArgs a)
 {
     constexpr int WARPS = kRowBlock / 32;
-    __shared__ dev::TileShared<WARPS> st;
-    __shared__ uint32_t s_src[kRowBlock];
-    __shared__ uint32_t s_dst[kRowBlock];
+    constexpr int TILE_WARPS = kRowsPerTile / 32;  // warps that own domain indices
+    __shared__ dev::TileShared<TILE_WARPS> st;
+    __shared__ uint32_t s_src[kRowsPerTile];
+    __shared__ uint32_t s_dst[kRowsPerTile];
 
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
@@ -43,20 +50,23 @@ __global__ void __launch_bounds__(kRowBlock) rows_tile_kernel(const __grid_const
         }
         return;
     }
-    const uint32_t i = tile * static_cast<uint32_t>(kRowBlock) + threadIdx.x;
-
-    uint32_t left[1] = {i >> a.g.R};
-    uint32_t right[1] = {i & a.g.rmask};
-    dev::cipher_items<ODD, 1>(left, right, a.keys, a.rounds, a.g);
-    const uint32_t src = (left[0] << a.g.R) | right[0];
-    bool keep = static_cast<uint64_t>(i) < a.g.domain && src < a.g.n;
-
-    const uint32_t mask = __ballot_sync(kFull, keep);
-    if (lane == 0) st.counts[warp] = __popc(mask);
+    const bool owner = warp < static_cast<uint32_t>(TILE_WARPS);
+    const uint32_t i = tile * static_cast<uint32_t>(kRowsPerTile) + threadIdx.x;
+    bool keep = false;
+    uint32_t src = 0, mask = 0;
+    if (owner) {
+        uint32_t left[1] = {i >> a.g.R};
+        uint32_t right[1] = {i & a.g.rmask};
+        dev::cipher_items<ODD, 1>(left, right, a.keys, a.rounds, a.g);
+        src = (left[0] << a.g.R) | right[0];
+        keep = static_cast<uint64_t>(i) < a.g.domain && src < a.g.n;
+        mask = __ballot_sync(kFull, keep);
+        if (lane == 0) st.counts[warp] = __popc(mask);
+    }
     __syncthreads();
     if (warp == 0)
-        dev::tile_scan_lookback<WARPS>(st, dev::StatusRing{a.status, ~0ull, 63u, tag}, tile, 0, a.timeout_ns,
-                                         a.skip_publish_tile, a.ws);
+        dev::tile_scan_lookback<TILE_WARPS>(st, dev::StatusRing{a.status, ~0ull, 63u, tag}, tile, 0, a.timeout_ns,
+                                              a.skip_publish_tile, a.ws);
     __syncthreads();
     const uint32_t prefix = st.prefix;
     const uint32_t count = st.aggregate;
@@ -84,18 +94,19 @@ __global__ void __launch_bounds__(kRowBlock) rows_tile_kernel(const __grid_const
             const uint64_t to_row = MODE == Mode::Gather ? s_dst[r] : s;
             const uint4 *from = in + from_row * chunks;
             uint4 *to = out + to_row * chunks;
-            uint32_t c = lane;
-            for (; c + 96u < chunks; c += 128u) {
-                const uint4 v0 = __ldg(from + c);
-                const uint4 v1 = __ldg(from + c + 32u);
-                const uint4 v2 = __ldg(from + c + 64u);
-                const uint4 v3 = __ldg(from + c + 96u);
-                to[c] = v0;
-                to[c + 32u] = v1;
-                to[c + 64u] = v2;
-                to[c + 96u] = v3;
+            for (uint32_t c0 = 0; c0 < chunks; c0 += 32u * kRowChunkUnroll) {
+                uint4 v[kRowChunkUnroll];
+#pragma unroll
+                for (int u = 0; u < kRowChunkUnroll; ++u) {
+                    const uint32_t c = c0 + static_cast<uint32_t>(u) * 32u + lane;
+                    if (c < chunks) v[u] = __ldg(from + c);
+                }
+#pragma unroll
+                for (int u = 0; u < kRowChunkUnroll; ++u) {
+                    const uint32_t c = c0 + static_cast<uint32_t>(u) * 32u + lane;
+                    if (c < chunks) to[c] = v[u];
+                }
             }
-            for (; c < chunks; c += 32u) to[c] = __ldg(from + c);
         }
     }
     if (threadIdx.x == 0) dev::finish_launch(a.ws, tag, gridDim.x);
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(kRowBlock) rows_tile_kernel(const __grid_const
 
 }  // namespace
 
-uint32_t rows_tile_size() { return static_cast<uint32_t>(kRowBlock); }
+uint32_t rows_tile_size() { return static_cast<uint32_t>(kRowsPerTile); }
 
 cudaError_t launch_rows(const TileArgs &a, Mode mode, cudaStream_t stream)
 {

@@ -6,11 +6,11 @@
 // seed0 + s (slot j holds player f(i_j)).  The player whose weight takes the
 // running total of the players before it from below q to at least q is
 // pivotal; counts[player] is incremented.  counts / samples estimates the
-// Shapley values.  A CTA owns whole samples: it walks the sample's domain in
-// chunks of BLOCK * ITEMS indices in increasing order, forms the running
-// weight with a block scan plus a carry (no inter-CTA communication), and
-// stops after the chunk in which the total reaches q.  The order itself never
-// leaves registers.
+// Shapley values.  One warp owns one sample at a time: it walks the sample's
+// domain in chunks of 32 * ITEMS indices in increasing order, forms the
+// running weight with warp scans plus a carry (no block barrier, no
+// inter-warp communication), and stops once the total reaches q.  The order
+// itself never leaves registers.
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -22,81 +22,47 @@ namespace {
 using dev::kFull;
 
 constexpr int kSvBlock = 256;
-constexpr int kSvItems = 8;
 constexpr int kSvWarps = kSvBlock / 32;
-constexpr uint32_t kSvChunk = kSvBlock * kSvItems;
+constexpr int kSvItems = 8;
+constexpr uint32_t kSvChunk = 32 * kSvItems;
 
 template <bool ODD>
 __global__ void __launch_bounds__(kSvBlock) shapley_voting_kernel(const __grid_constant__ ShapleyArgs a)
 {
-    constexpr int E = kSvItems * kSvWarps;
-    constexpr int C = (E + 31) / 32;
-    __shared__ uint32_t s_keys[kMaxRounds];
-    __shared__ uint64_t s_part[E];  // per (item, warp) weight sums, then their exclusive offsets
-    __shared__ uint64_t s_chunk;    // weight of the kept players of the chunk
-
+    __shared__ uint32_t s_keys[kSvWarps][kMaxRounds];
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
     const Geometry &g = a.g;
+    uint32_t *keys = s_keys[warp];
 
-    for (uint64_t smp = blockIdx.x; smp < a.samples; smp += gridDim.x) {
-        for (uint32_t r = threadIdx.x; r < a.rounds; r += kSvBlock) s_keys[r] = dev::splitmix_key(a.seed0 + smp, r);
-        __syncthreads();
+    for (uint64_t smp = static_cast<uint64_t>(blockIdx.x) * kSvWarps + warp; smp < a.samples;
+         smp += static_cast<uint64_t>(gridDim.x) * kSvWarps) {
+        for (uint32_t r = lane; r < a.rounds; r += 32) keys[r] = dev::splitmix_key(a.seed0 + smp, r);
+        __syncwarp();
         uint64_t carry = 0;  // weight of every kept player of the earlier chunks
         for (uint64_t base = 0; base < g.domain && carry < a.quota; base += kSvChunk) {
             uint32_t left[kSvItems], right[kSvItems];
 #pragma unroll
             for (int j = 0; j < kSvItems; ++j) {
-                const uint32_t i = static_cast<uint32_t>(base) + static_cast<uint32_t>(j * kSvBlock) + threadIdx.x;
+                const uint32_t i = static_cast<uint32_t>(base) + static_cast<uint32_t>(j * 32) + lane;
                 left[j] = i >> g.R;
                 right[j] = i & g.rmask;
             }
-            dev::cipher_items<ODD, kSvItems>(left, right, s_keys, a.rounds, g);
-            uint32_t player[kSvItems], wt[kSvItems];
-            uint64_t incl[kSvItems];
+            dev::cipher_items<ODD, kSvItems>(left, right, keys, a.rounds, g);
 #pragma unroll
             for (int j = 0; j < kSvItems; ++j) {
-                const uint64_t i = base + static_cast<uint64_t>(j * kSvBlock) + threadIdx.x;
-                player[j] = (left[j] << g.R) | right[j];
-                const bool keep = i < g.domain && player[j] < g.n;
-                wt[j] = keep ? a.w[player[j]] : 0u;
-                if (!keep) player[j] = 0xffffffffu;
+                const uint64_t i = base + static_cast<uint64_t>(j * 32) + lane;
+                const uint32_t player = (left[j] << g.R) | right[j];
+                const bool keep = i < g.domain && player < g.n;
+                const uint32_t wt = keep ? a.w[player] : 0u;
+                const uint64_t incl = dev::warp_inclusive_scan64(wt);
+                const uint64_t before = carry + incl - wt;
+                if (keep && before < a.quota && before + wt >= a.quota)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.counts + player), 1ull);
+                carry += __shfl_sync(kFull, incl, 31);
             }
-#pragma unroll
-            for (int j = 0; j < kSvItems; ++j) {
-                incl[j] = dev::warp_inclusive_scan64(wt[j]);
-                if (lane == 31) s_part[j * kSvWarps + warp] = incl[j];
-            }
-            __syncthreads();
-            if (warp == 0) {
-                uint64_t local[C];
-                uint64_t sum = 0;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const int e = static_cast<int>(lane) * C + c;
-                    local[c] = e < E ? s_part[e] : 0ull;
-                    sum += local[c];
-                }
-                const uint64_t total = dev::warp_inclusive_scan64(sum);
-                uint64_t run = total - sum;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const int e = static_cast<int>(lane) * C + c;
-                    if (e < E) s_part[e] = run;
-                    run += local[c];
-                }
-                if (lane == 31) s_chunk = total;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < kSvItems; ++j) {
-                const uint64_t before = carry + s_part[j * kSvWarps + warp] + incl[j] - wt[j];
-                if (player[j] < g.n && before < a.quota && before + wt[j] >= a.quota)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.counts + player[j]), 1ull);
-            }
-            carry += s_chunk;
-            __syncthreads();
         }
+        __syncwarp();  // every lane is done with the keys before the next sample's
     }
 }
 
@@ -118,7 +84,8 @@ cudaError_t launch_shapley_voting(const ShapleyArgs &a, cudaStream_t stream)
         per_sm[device] = (blocks > 0 ? blocks : 1) * sms;
     }
     const uint64_t cap = static_cast<uint64_t>(per_sm[device]);
-    const unsigned grid = static_cast<unsigned>(a.samples < cap ? a.samples : cap);
+    const uint64_t want = (a.samples + kSvWarps - 1) / kSvWarps;  // one warp per sample
+    const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
     if (a.g.k & 1u)
         shapley_voting_kernel<true><<<grid, kSvBlock, 0, stream>>>(a);
     else

@@ -143,3 +143,32 @@ def test_withheld_tile_times_out_and_recovers(bs):
     y = bs.permute(x, 3)
     assert bs.get_error() == 0
     assert np.array_equal(y.cpu().numpy(), oracle.permute(np.arange(n, dtype=np.int64), 3))
+
+
+def test_graph_capture_replays(bs):
+    # the pipelined kernel inside a captured CUDA graph: the workspace header
+    # is reset by the last CTA of every launch, so replays stay exact
+    n = 1_000_003
+    x = torch.from_numpy(_payload(n, 8, 12).view(np.int64)).cuda()
+    want = bs.permute(x, 21)
+    want_idx = bs.indices(n, 21, dtype=torch.int32)
+    y = torch.empty_like(x)
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        # the first call on this stream creates its workspace, before capture
+        bs.bshuffle_permute(x.data_ptr(), y.data_ptr(), n, 8, 21, 24, s.cuda_stream)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            bs.bshuffle_permute(x.data_ptr(), y.data_ptr(), n, 8, 21, 24, s.cuda_stream)
+            bs.bshuffle_indices(idx.data_ptr(), 4, n, 21, 24, s.cuda_stream)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        y.zero_()
+        idx.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y, want)
+        assert torch.equal(idx, want_idx)
+    assert bs.get_error() == 0
