@@ -1,0 +1,100 @@
+"""Maximum sizes: n = 2^32 - 1, the library's largest length (domain 2^32,
+k = 32, 16-bit halves), and n = 2^31, the largest length the staged path
+takes.  At n = 2^32 - 1 exactly one domain index is dropped, d = f^-1(n),
+so slot j holds X[f(j)] for j < d and X[f(j + 1)] for j >= d: sampled slots
+are checked against the oracle's bijection and inverse, and sums and extrema
+check that the output is a permutation of the input."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests.gpu_helpers import assert_no_device_error
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N_MAX = 2**32 - 1
+
+
+@pytest.fixture(scope="module")
+def bs():
+    from paper_2106_06161_gb300 import build
+    build.build()
+    import paper_2106_06161_gb300
+    paper_2106_06161_gb300.load()
+    yield paper_2106_06161_gb300
+    paper_2106_06161_gb300.bshuffle_set_strategy(paper_2106_06161_gb300.BSHUFFLE_STRATEGY_AUTO)
+    torch.cuda.empty_cache()
+
+
+def _expected_sources(js: np.ndarray, seed: int) -> np.ndarray:
+    keys = oracle.round_keys(seed, 24)
+    d = int(oracle.varphilox_inverse(np.array([N_MAX], dtype=np.uint64), 32, keys)[0])
+    i = js.astype(np.uint64) + (js.astype(np.uint64) >= np.uint64(d)).astype(np.uint64)
+    return oracle.varphilox(i, 32, keys)
+
+
+def _sample_slots(seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.concatenate([np.arange(4096), rng.integers(0, N_MAX, 200_000), np.arange(N_MAX - 4096, N_MAX)])
+
+
+def test_max_length_uint32_iota(bs):
+    # 4-byte elements go through the pipelined kernel; x[i] = i, so the
+    # output is the index sequence itself (16 GiB in, 16 GiB out)
+    seed = 17
+    x = torch.arange(N_MAX, dtype=torch.int64, device="cuda").to(torch.int32)
+    y = bs.permute(x, seed)
+    assert_no_device_error()
+    js = _sample_slots(seed)
+    got = y[torch.from_numpy(js).cuda()].cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(got, _expected_sources(js, seed))
+    # a permutation of 0 .. n - 1: same sum, same extrema
+    yy = y.view(torch.int32)
+    total = int(yy.to(torch.int64).remainder(2**32).sum())
+    assert total == N_MAX * (N_MAX - 1) // 2
+    del x, yy, y
+    torch.cuda.empty_cache()
+
+
+def test_max_length_bytes_and_indices(bs):
+    # 1-byte elements (the plain kernel) and the 32-bit index output
+    seed = 5
+    idx = bs.indices(N_MAX, seed, dtype=torch.int32)
+    assert_no_device_error()
+    js = _sample_slots(seed + 1)
+    src = _expected_sources(js, seed)
+    got = idx[torch.from_numpy(js).cuda()].cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(got, src)
+    del idx
+    torch.cuda.empty_cache()
+    g = torch.Generator(device="cuda").manual_seed(3)
+    x = torch.randint(0, 256, (N_MAX,), dtype=torch.uint8, device="cuda", generator=g)
+    y = bs.permute(x, seed)
+    assert_no_device_error()
+    assert torch.equal(y[torch.from_numpy(js).cuda()].cpu(), x[torch.from_numpy(src.astype(np.int64)).cuda()].cpu())
+    assert torch.equal(torch.bincount(y, minlength=256), torch.bincount(x, minlength=256))
+    del x, y
+    torch.cuda.empty_cache()
+
+
+def test_largest_staged_length(bs):
+    # n = 2^31 uint32 through the staged path in both directions
+    n, seed = 2**31, 9
+    x = torch.arange(n, dtype=torch.int64, device="cuda").to(torch.int32)
+    bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_STAGED)
+    try:
+        y = bs.permute(x, seed)
+        assert_no_device_error()
+        rng = np.random.default_rng(8)
+        js = np.concatenate([np.arange(2048), rng.integers(0, n, 200_000), np.arange(n - 2048, n)])
+        src = oracle.varphilox(js.astype(np.uint64), 31, oracle.round_keys(seed, 24))
+        got = y[torch.from_numpy(js).cuda()].cpu().numpy().view(np.uint32).astype(np.uint64)
+        assert np.array_equal(got, src)
+        z = bs.inverse(y, seed)
+        assert_no_device_error()
+        assert torch.equal(z, x)
+    finally:
+        bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
+    del x, y, z
+    torch.cuda.empty_cache()
