@@ -9,11 +9,13 @@
 //
 //   compute warps, iteration i (buffer i % 2): take a ticket, evaluate the
 //     bijection, start copying the kept elements X[f(i)] into the buffer
-//     with cp.async (one copy group per thread and tile), store the keep
-//     ballots and publish the tile aggregate (the last compute warp to add
-//     its count does it); then store tile i - 1: wait for its rank (look-back
-//     warp) and for this thread's own copy group of that tile, and write each
-//     element this thread gathered to its slot.
+//     with cp.async (one copy group per thread and tile; the index and
+//     scatter modes store the image itself), store the keep ballots and
+//     publish the tile aggregate (the last compute warp to add its count
+//     does it); then store tile i - 1: wait for its rank (look-back warp)
+//     and for this thread's own copy group of that tile, and write each
+//     element this thread gathered to its slot (scatter: read the element of
+//     that slot and write it to the image).
 //   look-back warp, tile i: wait for the ballots, form the in-tile offsets,
 //     look back, publish the inclusive prefix and hand the prefix to the
 //     compute warps.

@@ -60,7 +60,10 @@ def test_max_length_uint32_iota(bs):
 def test_max_length_bytes_and_indices(bs):
     # 1-byte elements (the plain kernel) and the 32-bit index output
     seed = 5
-    idx = bs.indices(N_MAX, seed, dtype=torch.int32)
+    # unsigned 32-bit indices through the C ABI (the tensor wrapper only
+    # hands out signed int32 up to 2^31)
+    idx = torch.empty(N_MAX, dtype=torch.int32, device="cuda")
+    bs.bshuffle_indices(idx.data_ptr(), 4, N_MAX, seed, 24, torch.cuda.current_stream().cuda_stream)
     assert_no_device_error()
     js = _sample_slots(seed + 1)
     src = _expected_sources(js, seed)
