@@ -246,8 +246,12 @@ FORWARD_OPS_PER_EVAL = 24 * 5
 INVERSE_OPS_PER_EVAL = 24 * 7
 
 
-def roofline_for(passes, bsbuild, strategy):
-    """Roofline of the dominant kernel of one step, plus every pass's line."""
+def roofline_for(passes, bsbuild, strategy, window_scatter_ms=None):
+    """Roofline of the dominant kernel of one step, plus every pass's line.
+
+    The staged scatter pass also gets its fraction of the window-scatter
+    kernel (the same sequential reads and random writes into 8 MiB windows
+    with nothing else), the L2 random-write ceiling it runs into."""
     peak, peak_kind = measured_peaks()
     n, k = N_MAIN, 28
     if len(passes) == 1 and strategy == STRATEGIES["single_pass"]:
@@ -274,6 +278,10 @@ def roofline_for(passes, bsbuild, strategy):
                     "frac": achieved / peak, "algorithmic_bytes_per_launch": work,
                     "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
         line["traffic"] = traffic_for(name, bsbuild.kernel_fingerprint(src))
+        if name.startswith("staged_scatter") and window_scatter_ms:
+            line["window_scatter_ms"] = window_scatter_ms
+            line["l2_random_writes_per_s"] = n / (ms * 1e-3)
+            line["frac_of_window_scatter"] = window_scatter_ms / ms
         lines.append(line)
     dom = max(lines, key=lambda d: d["ms"])
     roof = {key: dom[key] for key in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
@@ -338,14 +346,20 @@ def run_ours(args):
         pass_ms.append(bs.bshuffle_last_pass_ms(sptr))
     bs.bshuffle_set_pass_timing(False)
     passes = [statistics.mean(col) for col in zip(*pass_ms)]
-    roofline, pass_lines = roofline_for(passes, bsbuild, bs.bshuffle_get_strategy())
-
-    e2e = e2e_pipeline(bs, torch, dev, host, seed, args, world)
     # the round trip is exact
     if rank == 0:
         idx = torch.randint(0, N_MAIN, (1 << 16,), device=dev)
         src = bs.indices(N_MAIN, seed)[idx]
         assert torch.equal(y[idx], x[src]), "shuffle output does not match its index sequence"
+    # the ceiling of the staged scatter pass, live: sequential reads and
+    # random writes inside 8 MiB windows (2^20 uint64), nothing else
+    ws = lambda: bs.bshuffle_window_scatter(xp, yp, N_MAIN, ELEM, 20, sptr)  # noqa: E731
+    for _ in range(3):
+        ws()
+    _, ws_region = timed_launches(ws, 10, stream, torch)
+    roofline, pass_lines = roofline_for(passes, bsbuild, bs.bshuffle_get_strategy(), ws_region / 10)
+
+    e2e = e2e_pipeline(bs, torch, dev, host, seed, args, world)
 
     extra = {}
     if not args.no_extra and rank == 0:

@@ -223,6 +223,19 @@ int bshuffle_shapley_voting(const uint32_t *weights, uint64_t n, uint64_t quota,
 int bshuffle_random_gather(const void *in, void *out, uint64_t n, uint32_t elem_bytes, void *stream);
 
 /*
+ * Measurement kernel, not a shuffle API: for every i, out[w 2^m + h_m(i -
+ * w 2^m)] = in[i] with window w = i >> m and h_m the bijection of
+ * bshuffle_random_gather on m = window_log2 bits.  Sequential reads and
+ * random writes confined to windows of 2^m elements: the access pattern of
+ * the staged path's second pass, so it measures the rate at which the L2
+ * takes random writes into a resident window (the bound of that pass).
+ * n must be a power of two in [16, 2^32], 4 <= window_log2 <= log2 n;
+ * elem_bytes 4, 8 or 16; BSHUFFLE_ERR_INVALID otherwise.
+ */
+int bshuffle_window_scatter(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint32_t window_log2,
+                            void *stream);
+
+/*
  * GPU helpers for the statistical tests of Sec. 5 (not part of the shuffle).
  * bshuffle_kendall_pairs: for each p < num_pairs, out[p] = n_dis(s, t) of the
  * permutations s = perms[2p], t = perms[2p + 1] (rows of n uint32 ranks),

@@ -33,6 +33,7 @@ from ._lib import (
     bshuffle_permute,
     bshuffle_shapley_voting,
     bshuffle_random_gather,
+    bshuffle_window_scatter,
     bshuffle_release_workspaces,
     bshuffle_round_keys,
     bshuffle_set_lookback_timeout_ns,
@@ -67,7 +68,7 @@ __all__ = [
     "BSHUFFLE_STRATEGY_STAGED", "BSHUFFLE_STRATEGY_PIPELINED",
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
     "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",
-    "bshuffle_shapley_voting", "shapley_voting",
+    "bshuffle_shapley_voting", "shapley_voting", "bshuffle_window_scatter",
 ]
 
 

@@ -52,6 +52,7 @@ SIGNATURES = {
     "bshuffle_permute_static": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
     "bshuffle_mc_group_diff": (_int, [_p, _u64, _u64, _u64, _u32, _u32, _p, _p]),
     "bshuffle_shapley_voting": (_int, [_p, _u64, _u64, _u64, _u64, _u32, _p, _p]),
+    "bshuffle_window_scatter": (_int, [_p, _p, _u64, _u32, _u32, _p]),
     "bshuffle_random_gather": (_int, [_p, _p, _u64, _u32, _p]),
     "bshuffle_set_strategy": (_int, [_int]),
     "bshuffle_get_strategy": (_int, []),
@@ -142,6 +143,12 @@ def bshuffle_shapley_voting(w_ptr: int, n: int, quota: int, seed0: int, samples:
                             counts_ptr: int, stream: int = 0) -> None:
     _check(load().bshuffle_shapley_voting(w_ptr, n, quota, seed0 & (2**64 - 1), samples, rounds, counts_ptr, stream),
            "bshuffle_shapley_voting")
+
+
+def bshuffle_window_scatter(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, window_log2: int,
+                            stream: int = 0) -> None:
+    _check(load().bshuffle_window_scatter(in_ptr, out_ptr, n, elem_bytes, window_log2, stream),
+           "bshuffle_window_scatter")
 
 
 def bshuffle_random_gather(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, stream: int = 0) -> None:

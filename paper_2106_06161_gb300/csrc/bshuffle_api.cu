@@ -633,6 +633,22 @@ int bshuffle_random_gather(const void *in, void *out, uint64_t n, uint32_t elem_
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 
+int bshuffle_window_scatter(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint32_t window_log2,
+                            void *stream)
+{
+    if (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16) return BSHUFFLE_ERR_ELEM;
+    if (n == 0) return BSHUFFLE_OK;
+    if (n < 16 || n > (uint64_t{1} << 32) || (n & (n - 1)) != 0) return BSHUFFLE_ERR_INVALID;
+    uint32_t k = 0;
+    while ((uint64_t{1} << k) < n) ++k;
+    if (window_log2 < 4 || window_log2 > k) return BSHUFFLE_ERR_INVALID;
+    const int rc = check_buffers(in, out, n, elem_bytes);
+    if (rc != BSHUFFLE_OK) return rc;
+    const cudaError_t e =
+        bsh::launch_window_scatter(in, out, k, window_log2, elem_bytes, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
 int bshuffle_kendall_pairs(const uint32_t *perms, uint32_t n, uint64_t num_pairs, uint64_t *out, void *stream)
 {
     if (num_pairs == 0) return BSHUFFLE_OK;

@@ -224,5 +224,7 @@ cudaError_t launch_shapley_voting(const ShapleyArgs &a, cudaStream_t stream);
 
 // Measurement kernel: out[i] = in[h(i)], n = 2^k, elem_bytes 4, 8 or 16.
 cudaError_t launch_random_gather(const void *in, void *out, uint32_t k, uint32_t elem_bytes, cudaStream_t stream);
+cudaError_t launch_window_scatter(const void *in, void *out, uint32_t k, uint32_t m, uint32_t elem_bytes,
+                                  cudaStream_t s);
 
 }  // namespace bsh

@@ -260,6 +260,23 @@ def test_random_gather_measurement_kernel(width):
         assert np.array_equal(to_host(out, x), x[_scramble(np.arange(n), k).astype(np.int64)])
 
 
+@pytest.mark.parametrize("width", [4, 8, 16])
+def test_window_scatter_measurement_kernel(width):
+    # out[w 2^m + h_m(i mod 2^m)] = in[i]: a permutation inside every window
+    for k, m in ((4, 4), (12, 8), (20, 16), (20, 20)):
+        n = 2**k
+        x = _payload(n, width, k + m)
+        xd = to_device(x)
+        out = torch.empty_like(xd)
+        bs.bshuffle_window_scatter(xd.data_ptr(), out.data_ptr(), n, width, m, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        i = np.arange(n)
+        dst = (i >> m << m) + _scramble(i & ((1 << m) - 1), m).astype(np.int64)
+        want = np.empty_like(x)
+        want[dst] = x
+        assert np.array_equal(to_host(out, x), want), (k, m)
+
+
 @pytest.mark.parametrize("width", [1, 4, 8, 16])
 def test_lcg_variant_matches_oracle(width):
     for n in (1, 5, 17, 2049, 65537, 1_000_003):
