@@ -240,7 +240,7 @@ def traffic_for(kernel: str, fingerprint: str):
 # lanes at the 2070 MHz maximum clock, over the operations one evaluation
 # needs as written (24 rounds; per even-k round the forward cipher takes two
 # product words, two XORs and one AND = 5, the inverse one more product word
-# and one more AND = 7), see the design doc.
+# and one more AND = 7).
 SMS, LANES_PER_SM, SM_HZ = 152, 128, 2.07e9
 FORWARD_OPS_PER_EVAL = 24 * 5
 INVERSE_OPS_PER_EVAL = 24 * 7
