@@ -35,15 +35,23 @@ using dev::kFull;
 
 constexpr int kSBlock = 256;
 constexpr int kSItems = 8;
-constexpr int kSWarps = kSBlock / 32;
-constexpr uint32_t kSTile = kSBlock * kSItems;
+constexpr uint32_t kSTile = kSBlock * kSItems;  // entries per CTA of P2
+// P1's CTA size (overridable at build time for tuning experiments): a P1 CTA
+// buckets kP1Block * kSItems consecutive elements.
+#ifndef BSHUFFLE_STAGED_P1_BLOCK
+#define BSHUFFLE_STAGED_P1_BLOCK 256
+#endif
+constexpr int kP1Block = BSHUFFLE_STAGED_P1_BLOCK;
+constexpr int kP1Warps = kP1Block / 32;
+constexpr uint32_t kP1Tile = kP1Block * kSItems;
+constexpr uint32_t kStagedMinChunk = kP1Tile > kSTile ? kP1Tile : kSTile;
 
-// Exclusive scan of cnt[0..m) into start[0..m) by the whole CTA (kSBlock threads).
+// Exclusive scan of cnt[0..m) into start[0..m) by the whole CTA (kP1Block threads).
 __device__ __forceinline__ void block_exclusive_scan(const uint32_t *cnt, uint32_t *start, uint32_t m,
                                                      uint32_t *s_warp)
 {
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const uint32_t per = (m + kSBlock - 1) / kSBlock;
+    const uint32_t per = (m + kP1Block - 1) / kP1Block;
     const uint32_t b0 = tid * per;
     const uint32_t b1 = b0 + per < m ? b0 + per : m;
     uint32_t sum = 0;
@@ -52,9 +60,9 @@ __device__ __forceinline__ void block_exclusive_scan(const uint32_t *cnt, uint32
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const uint32_t w = lane < static_cast<uint32_t>(kSWarps) ? s_warp[lane] : 0u;
+        const uint32_t w = lane < static_cast<uint32_t>(kP1Warps) ? s_warp[lane] : 0u;
         const uint32_t wi = dev::warp_inclusive_scan(w);
-        if (lane < static_cast<uint32_t>(kSWarps)) s_warp[lane] = wi - w;
+        if (lane < static_cast<uint32_t>(kP1Warps)) s_warp[lane] = wi - w;
     }
     __syncthreads();
     uint32_t run = s_warp[warp] + incl - sum;
@@ -70,28 +78,30 @@ __device__ __forceinline__ void block_exclusive_scan(const uint32_t *cnt, uint32
 // FORWARD: element b goes to slot f(b) (the inverse shuffle) instead of
 // f^-1(b) (the shuffle).
 template <class T, bool ODD, bool FORWARD>
-__global__ void __launch_bounds__(kSBlock) staged_bucket_kernel(const __grid_constant__ StagedArgs a)
+__global__ void __launch_bounds__(kP1Block) staged_bucket_kernel(const __grid_constant__ StagedArgs a)
 {
-    extern __shared__ uint32_t s_dyn[];  // 3 * num_dst words
-    uint32_t *s_cnt = s_dyn;
-    uint32_t *s_start = s_dyn + a.num_dst;
+    // dynamic shared memory: the chunk's sorted (value, position, bucket)
+    // staging, then three words per destination bucket
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    T *s_val = reinterpret_cast<T *>(s_raw);
+    uint32_t *s_pos = reinterpret_cast<uint32_t *>(s_raw + kP1Tile * sizeof(T));
+    uint16_t *s_bucket = reinterpret_cast<uint16_t *>(s_raw + kP1Tile * (sizeof(T) + 4));
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_raw + kP1Tile * (sizeof(T) + 6));
+    uint32_t *s_start = s_cnt + a.num_dst;
     uint32_t *s_gbase = s_start + a.num_dst;
-    __shared__ T s_val[kSTile];
-    __shared__ uint32_t s_pos[kSTile];
-    __shared__ uint16_t s_bucket[kSTile];
-    __shared__ uint32_t s_warp[kSWarps];
+    __shared__ uint32_t s_warp[kP1Warps];
 
     const uint32_t tid = threadIdx.x;
     const Geometry &g = a.g;
-    const uint32_t first = blockIdx.x * kSTile;  // n = 2^k is a multiple of kSTile
+    const uint32_t first = blockIdx.x * kP1Tile;  // n = 2^k is a multiple of kP1Tile
     const T *in = static_cast<const T *>(a.in);
-    for (uint32_t q = tid; q < a.num_dst; q += kSBlock) s_cnt[q] = 0u;
+    for (uint32_t q = tid; q < a.num_dst; q += kP1Block) s_cnt[q] = 0u;
 
     T val[kSItems];
     uint32_t left[kSItems], right[kSItems];
 #pragma unroll
     for (int j = 0; j < kSItems; ++j) {
-        const uint32_t b = first + static_cast<uint32_t>(j * kSBlock) + tid;
+        const uint32_t b = first + static_cast<uint32_t>(j * kP1Block) + tid;
         val[j] = __ldcs(in + b);
         left[j] = b >> g.R;
         right[j] = b & g.rmask;
@@ -112,7 +122,7 @@ __global__ void __launch_bounds__(kSBlock) staged_bucket_kernel(const __grid_con
     for (int j = 0; j < kSItems; ++j) slot[j] = atomicAdd(&s_cnt[bucket[j]], 1u);
     __syncthreads();
     block_exclusive_scan(s_cnt, s_start, a.num_dst, s_warp);
-    for (uint32_t q = tid; q < a.num_dst; q += kSBlock) {
+    for (uint32_t q = tid; q < a.num_dst; q += kP1Block) {
         const uint32_t c = s_cnt[q];
         s_gbase[q] = c != 0u ? atomicAdd(&a.dst_cursor[q], c) : 0u;
     }
@@ -127,7 +137,7 @@ __global__ void __launch_bounds__(kSBlock) staged_bucket_kernel(const __grid_con
     __syncthreads();
     T *dval = static_cast<T *>(a.dval);
     const uint64_t bsize = uint64_t{1} << a.dst_shift;
-    for (uint32_t p = tid; p < kSTile; p += kSBlock) {
+    for (uint32_t p = tid; p < kP1Tile; p += kP1Block) {
         const uint32_t q = s_bucket[p];
         const uint64_t off = static_cast<uint64_t>(s_gbase[q]) + (p - s_start[q]);
         const uint64_t bucket_base = static_cast<uint64_t>(q) << a.dst_shift;
@@ -172,6 +182,13 @@ __global__ void __launch_bounds__(kSBlock) staged_scatter_kernel(const __grid_co
     }
 }
 
+// P1's dynamic shared memory for num_dst destination buckets.
+template <class T>
+constexpr size_t p1_smem_bytes(uint32_t num_dst)
+{
+    return kP1Tile * (sizeof(T) + sizeof(uint32_t) + sizeof(uint16_t)) + 3u * num_dst * sizeof(uint32_t);
+}
+
 cudaError_t mark(cudaEvent_t *marks, int i, cudaStream_t stream)
 {
     return marks != nullptr ? cudaEventRecord(marks[i], stream) : cudaSuccess;
@@ -187,24 +204,26 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     if (!configured[device]) {
         e = cudaFuncSetAttribute(staged_bucket_kernel<T, true, FORWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 3 * 4096 * 4);
+                                 static_cast<int>(p1_smem_bytes<T>(4096)));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(staged_bucket_kernel<T, false, FORWARD>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 4);
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(p1_smem_bytes<T>(4096)));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(staged_scatter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(kScatterSmemReserve));
         if (e != cudaSuccess) return e;
         configured[device] = true;
     }
-    const size_t dyn = 3u * a.num_dst * sizeof(uint32_t);
+    const size_t dyn = p1_smem_bytes<T>(a.num_dst);
     const unsigned chunks = static_cast<unsigned>(static_cast<uint64_t>(a.g.n) / kSTile);
+    const unsigned p1_chunks = static_cast<unsigned>(static_cast<uint64_t>(a.g.n) / kP1Tile);
     e = mark(marks, 0, stream);
     if (e != cudaSuccess) return e;
     if (a.g.k & 1u)
-        staged_bucket_kernel<T, true, FORWARD><<<chunks, kSBlock, dyn, stream>>>(a);
+        staged_bucket_kernel<T, true, FORWARD><<<p1_chunks, kP1Block, dyn, stream>>>(a);
     else
-        staged_bucket_kernel<T, false, FORWARD><<<chunks, kSBlock, dyn, stream>>>(a);
+        staged_bucket_kernel<T, false, FORWARD><<<p1_chunks, kP1Block, dyn, stream>>>(a);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = mark(marks, 1, stream);
     if (e != cudaSuccess) return e;
@@ -216,13 +235,13 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
 
 }  // namespace
 
-uint32_t staged_tile_size() { return kSTile; }
+uint32_t staged_tile_size() { return kStagedMinChunk; }
 
 cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, bool inverse, cudaStream_t stream,
                           cudaEvent_t *marks)
 {
-    if (a.num_dst > 4096 || static_cast<uint64_t>(a.g.n) != a.g.domain || a.g.domain < 2 * kSTile ||
-        a.g.domain > (uint64_t{1} << 31) || (uint64_t{1} << a.dst_shift) < kSTile)
+    if (a.num_dst > 4096 || static_cast<uint64_t>(a.g.n) != a.g.domain || a.g.domain < 2 * kStagedMinChunk ||
+        a.g.domain > (uint64_t{1} << 31) || (uint64_t{1} << a.dst_shift) < kStagedMinChunk)
         return cudaErrorInvalidValue;
     switch (elem_bytes) {
     case 4: return inverse ? launch_typed<unsigned int, true>(a, stream, marks)
