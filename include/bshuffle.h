@@ -15,9 +15,11 @@
  * call: the bijection in registers, the compaction as an in-tile scan chained
  * across tiles by decoupled look-back (single pass, Sec. 4 last paragraph and
  * the "Bijective2" variant of Sec. 6), the gather of each kept element once,
- * and a coalesced store into its compacted slot.  For inputs much larger than
- * L2 and of power-of-two length, bshuffle_permute can instead run a staged
- * variant with the same output (see bshuffle_set_strategy).
+ * and a coalesced store into its compacted slot.  By default the single pass
+ * runs pipelined (a dedicated warp per CTA does the look-back while the other
+ * warps evaluate the next tile), and inputs much larger than L2 of
+ * power-of-two length run a staged two-pass variant; the output is the same
+ * (see bshuffle_set_strategy).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
