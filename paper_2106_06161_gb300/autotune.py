@@ -1,11 +1,15 @@
-"""Autotuner of the single-pass permute kernel.
+"""Autotuner of the plain single-pass permute kernel.
 
 For each element width (4, 8, 16 bytes) every configuration the library
 offers (CTA size, domain indices per thread, rounds unrolled at compile time;
 see bshuffle_tuning_describe) is timed with CUDA events on the current stream
 at a worst-case padded length (n = 2^k + 1: half of the 2^(k+1) domain is
 evaluated and dropped), and the fastest is selected.  Every configuration
-computes the same output; only speed differs.
+computes the same output; only speed differs.  The selection applies where
+the plain kernel runs: BSHUFFLE_STRATEGY_SINGLE_PASS, and 16-byte gathers
+under the default strategy (4- and 8-byte gathers default to the pipelined
+kernel, whose shape is fixed: three persistent CTAs of eight compute warps
+and one look-back warp per SM measured fastest).
 
 Results are cached as JSON keyed by device name, compute capability and SM
 count, then element width.  `apply_cached()` re-selects the cached choices in
