@@ -302,10 +302,9 @@ int bshuffle_release_workspaces(void);
  *       with the look-back.  Same memory traffic and workspace as the single
  *       pass.
  *   BSHUFFLE_STRATEGY_AUTO (default)  staged when it applies and
- *       n * elem_bytes >= 256 MiB; otherwise the pipelined single pass,
- *       except for gathers of 16-byte elements (plain single pass, faster
- *       there); if the staged workspace cannot be allocated the single pass
- *       runs instead.
+ *       n * elem_bytes >= 256 MiB; otherwise the pipelined single pass where
+ *       it applies, else the plain one; if the staged workspace cannot be
+ *       allocated the single pass runs instead.
  * The setting is process-wide.  Returns BSHUFFLE_ERR_INVALID for other values.
  */
 #define BSHUFFLE_STRATEGY_AUTO 0

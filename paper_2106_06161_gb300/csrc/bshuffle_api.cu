@@ -223,15 +223,13 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     a.timeout_ns = g_timeout_ns.load();
     fill_keys(seed, rounds, a.keys);
     const bool rows = (mode == Mode::Gather || mode == Mode::Scatter) && elem_bytes > 16;
-    // the pipelined kernel: on request for every call it serves, and by
-    // default where it measured faster than the plain kernel (all but
-    // gathers of 16-byte elements)
+    // the pipelined kernel: on request and by default, for every call it
+    // serves (it measured faster than the plain kernel for each of them)
     const int strategy = g_strategy.load();
-    const bool auto_pipe = !(mode == Mode::Gather && elem_bytes == 16);
     const bool pipe = !rows && bsh::pipe_supports(mode, elem_bytes) &&
                       (which == FusedKernel::Pipelined ||
                        (which == FusedKernel::ByStrategy &&
-                        (strategy == BSHUFFLE_STRATEGY_PIPELINED || (strategy == BSHUFFLE_STRATEGY_AUTO && auto_pipe))));
+                        (strategy == BSHUFFLE_STRATEGY_PIPELINED || strategy == BSHUFFLE_STRATEGY_AUTO)));
     const int config = rows ? 0 : bsh::elem_config_for(elem_bytes, mode, rounds);
     const uint64_t tile = rows ? bsh::rows_tile_size() : (pipe ? bsh::pipe_tile_size(elem_bytes) : bsh::elem_tile_size(config));
     const uint64_t tiles = (a.g.domain + tile - 1) / tile;
