@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kBBlock, min_ctas_for(sizeof(T))) batch_tile_k
 // it (look-back bounded by the instance's first tile).  After its stores,
 // warp 0 takes the next ticket and resolves its instance.  Tickets are taken
 // only when the CTA no longer waits on other tiles, and aggregates never wait
-// on a look-back.  Used for 4- and 8-byte elements.
+// on a look-back.  Used for 4-, 8- and 16-byte elements.
 constexpr int kPipeWarps = 8;
 constexpr int kPipeItems = kTile / (kPipeWarps * 32);
 static_assert(kPipeItems * kPipeWarps * 32 == static_cast<int>(kTile), "tile shape");
@@ -594,7 +594,7 @@ cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream)
     case 2: return launch_typed<unsigned short>(a, stream);
     case 4: return launch_pipe_typed<unsigned int>(a, stream);
     case 8: return launch_pipe_typed<unsigned long long>(a, stream);
-    case 16: return launch_typed<uint4>(a, stream);  // the plain kernel measured faster here
+    case 16: return launch_pipe_typed<uint4>(a, stream);
     default: return cudaErrorInvalidValue;
     }
 }
