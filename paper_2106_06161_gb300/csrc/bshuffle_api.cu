@@ -231,7 +231,7 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
                        (which == FusedKernel::ByStrategy &&
                         (strategy == BSHUFFLE_STRATEGY_PIPELINED || strategy == BSHUFFLE_STRATEGY_AUTO)));
     const int config = rows ? 0 : bsh::elem_config_for(elem_bytes, mode, rounds);
-    const uint64_t tile = rows ? bsh::rows_tile_size() : (pipe ? bsh::pipe_tile_size(elem_bytes) : bsh::elem_tile_size(config));
+    const uint64_t tile = rows ? bsh::rows_tile_size(elem_bytes) : (pipe ? bsh::pipe_tile_size(elem_bytes) : bsh::elem_tile_size(config));
     const uint64_t tiles = (a.g.domain + tile - 1) / tile;
     a.num_tiles = static_cast<uint32_t>(tiles);
     Workspace *ws = nullptr;

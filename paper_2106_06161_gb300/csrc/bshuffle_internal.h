@@ -83,7 +83,7 @@ int select_elem_config(uint32_t elem_bytes, int config);
 // Domain indices per tile of an element-kernel configuration and of the
 // row kernels.
 uint32_t elem_tile_size(int config);
-uint32_t rows_tile_size();
+uint32_t rows_tile_size(uint32_t row_bytes);
 
 // Enqueue one fused launch of num_tiles CTAs in configuration `config`.
 cudaError_t launch_elem(const TileArgs &a, Mode mode, uint32_t elem_bytes, int config, cudaStream_t stream);
