@@ -172,3 +172,44 @@ def test_graph_capture_replays(bs):
         assert torch.equal(y, want)
         assert torch.equal(idx, want_idx)
     assert bs.get_error() == 0
+
+
+def test_concurrent_streams_share_the_gpu(bs):
+    # Persistent kernels on three streams at once (pipelined single pass,
+    # batched, staged): while they share the SMs not every CTA of a launch is
+    # resident; tickets go only to running CTAs, so each still finishes, and
+    # each stream's workspace keeps the results exact.
+    n1 = 3_000_017
+    x1 = torch.from_numpy(_payload(n1, 8, 31).view(np.int64)).cuda()
+    sizes = workloads.batched_sizes(count=300, hi=200_000, seed=4)
+    data = torch.from_numpy(workloads.batched_payloads(sizes, seed=5)).cuda()
+    x3 = torch.from_numpy(workloads.uniform_u64(2**22, 6).view(np.int64)).cuda()
+    want1 = oracle.permute(x1.cpu().numpy().view(np.uint64), 9)
+    want3 = oracle.permute(x3.cpu().numpy().view(np.uint64), 10)
+    seeds = list(range(40, 40 + len(sizes)))
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    torch.cuda.synchronize()
+    for _ in range(3):
+        with torch.cuda.stream(streams[0]):
+            y1 = bs.permute(x1, 9)
+        with torch.cuda.stream(streams[1]):
+            y2 = bs.batched_packed(data, sizes, seeds)
+        with torch.cuda.stream(streams[2]):
+            bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_STAGED)
+            try:
+                y3 = bs.permute(x3, 10)
+            finally:
+                bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_PIPELINED)
+        torch.cuda.synchronize()
+        for s in streams:
+            with torch.cuda.stream(s):
+                assert bs.get_error() == 0
+        assert np.array_equal(y1.cpu().numpy().view(np.uint64), want1)
+        assert np.array_equal(y3.cpu().numpy().view(np.uint64), want3)
+        host = data.cpu().numpy()
+        res = y2.cpu().numpy()
+        off = 0
+        for t in (0, 1, len(sizes) // 2, len(sizes) - 1):
+            off = int(np.sum(sizes[:t]))
+            m = int(sizes[t])
+            assert np.array_equal(res[off:off + m], oracle.permute(host[off:off + m], seeds[t])), t
