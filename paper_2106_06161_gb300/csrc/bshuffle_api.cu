@@ -31,8 +31,6 @@ std::atomic<int> g_strategy{BSHUFFLE_STRATEGY_AUTO};
 std::atomic<int> g_pass_timing{0};
 // Auto strategy: the staged path from this many input bytes on.
 constexpr uint64_t kStagedMinBytes = uint64_t{1} << 28;
-// Input/output window of one staged bucket.
-constexpr uint64_t kStagedWindowBytes = uint64_t{1} << 23;
 
 // ------------------------------------------------------------------ host math
 
@@ -302,10 +300,7 @@ int run_staged(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint6
     if (a.g.domain != n) return BSHUFFLE_ERR_INVALID;
     a.rounds = rounds;
     fill_keys(seed, rounds, a.keys);
-    const uint32_t lg = ceil_log2(n);
-    uint32_t shift = ceil_log2(kStagedWindowBytes / elem_bytes);
-    if (lg > 12 && lg - 12 > shift) shift = lg - 12;  // at most 4096 buckets
-    if (shift > lg) shift = lg;
+    const uint32_t shift = bsh::staged_window_shift(n, elem_bytes);
     a.dst_shift = shift;
     a.num_dst = static_cast<uint32_t>((n + (uint64_t{1} << shift) - 1) >> shift);
 

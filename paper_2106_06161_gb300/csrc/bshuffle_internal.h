@@ -149,6 +149,9 @@ struct StagedArgs {
 };
 
 uint32_t staged_tile_size();
+// log2 of the destination bucket (output window) in elements for a staged
+// shuffle of n = 2^k elements of elem_bytes.
+uint32_t staged_window_shift(uint64_t n, uint32_t elem_bytes);
 // Enqueue the two passes (elem_bytes 4, 8 or 16) of the shuffle, or of the
 // inverse shuffle when `inverse`; the caller zeroes the cursors first.
 // marks, when not null, are 3 events recorded before P1, between the passes

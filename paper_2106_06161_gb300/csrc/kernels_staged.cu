@@ -12,17 +12,26 @@
 // slot f^-1(b): the inverse cipher of Sec. 3.2 turns the gather into a
 // scatter whose source side is sequential.  Two passes:
 //
-//   P1  per chunk of 2,048 consecutive elements b: a coalesced read of X[b],
-//       the inverse cipher j = f^-1(b), and a counting sort of (value, j) by
-//       destination bucket (j >> dst_shift, an 8 MiB output window) in shared
-//       memory; each bucket's run is appended with one global atomic per
-//       bucket per chunk.
+//   P1  per chunk of 2,048 (or 4,096) consecutive elements b: a coalesced
+//       read of X[b], the inverse cipher j = f^-1(b), and a counting sort of
+//       (value, j) by destination bucket (j >> dst_shift, an output window of
+//       4 MiB or more) in shared memory; each bucket's run is appended with
+//       one global atomic per bucket per chunk.
 //   P2  per chunk of one destination bucket: out[j] = value, random within an
 //       L2-resident output window whose lines leave L2 complete.
 //
 // Runs are appended in a nondeterministic order, but every element is placed
 // by its exact slot, so the output is deterministic and identical to the
 // single pass.
+//
+// Sizes (measured on GB300): P2 is fastest in small windows (its random
+// writes stay in L2; 4 MiB beats 8 MiB by 13 %, 32 MiB costs 50 % more), while
+// P1 slows down steeply past 256 buckets per 2,048-element chunk (each chunk
+// zeroes, scans and atomically appends every bucket).  staged_window_shift
+// takes the smallest window (at least 4 MiB) that keeps the bucket count at
+// one per 8 elements of a P1 chunk, and inputs over 2 GiB of 4- or 8-byte
+// elements use 4,096-element chunks (16 items per thread), which halves the
+// appends per element and allows 512 buckets.
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -37,14 +46,23 @@ constexpr int kSBlock = 256;
 constexpr int kSItems = 8;
 constexpr uint32_t kSTile = kSBlock * kSItems;  // entries per CTA of P2
 // P1's CTA size (overridable at build time for tuning experiments): a P1 CTA
-// buckets kP1Block * kSItems consecutive elements.
+// buckets kP1Block * ITEMS consecutive elements, ITEMS = 8 or 16.
 #ifndef BSHUFFLE_STAGED_P1_BLOCK
 #define BSHUFFLE_STAGED_P1_BLOCK 256
 #endif
 constexpr int kP1Block = BSHUFFLE_STAGED_P1_BLOCK;
 constexpr int kP1Warps = kP1Block / 32;
-constexpr uint32_t kP1Tile = kP1Block * kSItems;
-constexpr uint32_t kStagedMinChunk = kP1Tile > kSTile ? kP1Tile : kSTile;
+constexpr uint32_t kP1TileSmall = kP1Block * 8;
+constexpr uint32_t kP1TileLarge = kP1Block * 16;
+constexpr uint32_t kStagedMinChunk = kP1TileSmall > kSTile ? kP1TileSmall : kSTile;
+constexpr uint32_t kMinWindowLog2 = 22;       // 4 MiB
+constexpr uint64_t kLargeInputBytes = uint64_t{1} << 31;  // above this, 16 items per P1 thread
+
+// P1 items per thread for n elements of elem_bytes.
+uint32_t p1_items_for(uint64_t n, uint32_t elem_bytes)
+{
+    return elem_bytes <= 8 && n * elem_bytes > kLargeInputBytes ? 16u : 8u;
+}
 
 // Exclusive scan of cnt[0..m) into start[0..m) by the whole CTA (kP1Block threads).
 __device__ __forceinline__ void block_exclusive_scan(const uint32_t *cnt, uint32_t *start, uint32_t m,
@@ -72,21 +90,25 @@ __device__ __forceinline__ void block_exclusive_scan(const uint32_t *cnt, uint32
     }
 }
 
-// Streaming read of data used once (evict-first in L1 and L2).
 // ------------------------------------------------------------------ P1
 
 // FORWARD: element b goes to slot f(b) (the inverse shuffle) instead of
-// f^-1(b) (the shuffle).
-template <class T, bool ODD, bool FORWARD>
+// f^-1(b) (the shuffle).  The round keys sit in kernel parameter space, so
+// the unrolled 24 rounds read them as constant operands.
+template <class T, bool ODD, bool FORWARD, int ITEMS>
 __global__ void __launch_bounds__(kP1Block) staged_bucket_kernel(const __grid_constant__ StagedArgs a)
 {
-    // dynamic shared memory: the chunk's sorted (value, position, bucket)
-    // staging, then three words per destination bucket
+    constexpr int kP1Items = ITEMS;
+    constexpr uint32_t kP1Tile = kP1Block * ITEMS;
+    // dynamic shared memory: the chunk's entries (value, output slot) sorted
+    // by destination bucket, then three words per destination bucket.  The
+    // bucket and the entry's staged offset are recomputed from the slot at
+    // write-out: 12 bytes per uint64 entry instead of 14 or 16 made this pass
+    // 3-9 % faster on GB300 (it is sensitive to its shared-memory footprint).
     extern __shared__ __align__(16) unsigned char s_raw[];
     T *s_val = reinterpret_cast<T *>(s_raw);
-    uint32_t *s_pos = reinterpret_cast<uint32_t *>(s_raw + kP1Tile * sizeof(T));
-    uint16_t *s_bucket = reinterpret_cast<uint16_t *>(s_raw + kP1Tile * (sizeof(T) + 4));
-    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_raw + kP1Tile * (sizeof(T) + 6));
+    uint32_t *s_dst = reinterpret_cast<uint32_t *>(s_raw + kP1Tile * sizeof(T));
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_raw + kP1Tile * (sizeof(T) + 4));
     uint32_t *s_start = s_cnt + a.num_dst;
     uint32_t *s_gbase = s_start + a.num_dst;
     __shared__ uint32_t s_warp[kP1Warps];
@@ -97,29 +119,25 @@ __global__ void __launch_bounds__(kP1Block) staged_bucket_kernel(const __grid_co
     const T *in = static_cast<const T *>(a.in);
     for (uint32_t q = tid; q < a.num_dst; q += kP1Block) s_cnt[q] = 0u;
 
-    T val[kSItems];
-    uint32_t left[kSItems], right[kSItems];
+    T val[kP1Items];
+    uint32_t left[kP1Items], right[kP1Items];
 #pragma unroll
-    for (int j = 0; j < kSItems; ++j) {
+    for (int j = 0; j < kP1Items; ++j) {
         const uint32_t b = first + static_cast<uint32_t>(j * kP1Block) + tid;
         val[j] = __ldcs(in + b);
         left[j] = b >> g.R;
         right[j] = b & g.rmask;
     }
     if constexpr (FORWARD)
-        dev::cipher_items<ODD, kSItems>(left, right, a.keys, a.rounds, g);
+        dev::cipher_items<ODD, kP1Items>(left, right, a.keys, a.rounds, g);
     else
-        dev::cipher_inverse_items<ODD, kSItems>(left, right, a.keys, a.rounds, g);
-    uint32_t bucket[kSItems], pos[kSItems], slot[kSItems];
+        dev::cipher_inverse_items<ODD, kP1Items>(left, right, a.keys, a.rounds, g);
+    uint32_t dst[kP1Items], slot[kP1Items];
 #pragma unroll
-    for (int j = 0; j < kSItems; ++j) {
-        const uint32_t dst = (left[j] << g.R) | right[j];  // f^-1(b) (or f(b)): the element's output slot
-        bucket[j] = dst >> a.dst_shift;
-        pos[j] = dst & ((1u << a.dst_shift) - 1u);
-    }
+    for (int j = 0; j < kP1Items; ++j) dst[j] = (left[j] << g.R) | right[j];  // f^-1(b) (or f(b)): its slot
     __syncthreads();  // s_cnt zeroed
 #pragma unroll
-    for (int j = 0; j < kSItems; ++j) slot[j] = atomicAdd(&s_cnt[bucket[j]], 1u);
+    for (int j = 0; j < kP1Items; ++j) slot[j] = atomicAdd(&s_cnt[dst[j] >> a.dst_shift], 1u);
     __syncthreads();
     block_exclusive_scan(s_cnt, s_start, a.num_dst, s_warp);
     for (uint32_t q = tid; q < a.num_dst; q += kP1Block) {
@@ -128,24 +146,26 @@ __global__ void __launch_bounds__(kP1Block) staged_bucket_kernel(const __grid_co
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSItems; ++j) {
-        const uint32_t p = s_start[bucket[j]] + slot[j];
+    for (int j = 0; j < kP1Items; ++j) {
+        const uint32_t p = s_start[dst[j] >> a.dst_shift] + slot[j];
         s_val[p] = val[j];
-        s_pos[p] = pos[j];
-        s_bucket[p] = static_cast<uint16_t>(bucket[j]);
+        s_dst[p] = dst[j];
     }
     __syncthreads();
     T *dval = static_cast<T *>(a.dval);
-    const uint64_t bsize = uint64_t{1} << a.dst_shift;
-    for (uint32_t p = tid; p < kP1Tile; p += kP1Block) {
-        const uint32_t q = s_bucket[p];
-        const uint64_t off = static_cast<uint64_t>(s_gbase[q]) + (p - s_start[q]);
-        const uint64_t bucket_base = static_cast<uint64_t>(q) << a.dst_shift;
+    const uint32_t bsize = 1u << a.dst_shift;
+#pragma unroll
+    for (int j = 0; j < kP1Items; ++j) {
+        const uint32_t p = static_cast<uint32_t>(j * kP1Block) + tid;
+        const uint32_t d = s_dst[p];
+        const uint32_t q = d >> a.dst_shift;
+        const uint32_t off = s_gbase[q] + (p - s_start[q]);
         if (off < bsize) {
-            dval[bucket_base + off] = s_val[p];
-            a.dpos[bucket_base + off] = s_pos[p];
+            const uint32_t o = (q << a.dst_shift) + off;
+            dval[o] = s_val[p];
+            a.dpos[o] = d & (bsize - 1u);
         } else {
-            dev::record_error(a.ws, dev::kErrDeviceBounds, bucket_base + off);
+            dev::record_error(a.ws, dev::kErrDeviceBounds, (static_cast<uint64_t>(q) << a.dst_shift) + off);
         }
     }
 }
@@ -183,10 +203,10 @@ __global__ void __launch_bounds__(kSBlock) staged_scatter_kernel(const __grid_co
 }
 
 // P1's dynamic shared memory for num_dst destination buckets.
-template <class T>
+template <class T, int ITEMS>
 constexpr size_t p1_smem_bytes(uint32_t num_dst)
 {
-    return kP1Tile * (sizeof(T) + sizeof(uint32_t) + sizeof(uint16_t)) + 3u * num_dst * sizeof(uint32_t);
+    return size_t{kP1Block} * ITEMS * (sizeof(T) + sizeof(uint32_t)) + 3u * num_dst * sizeof(uint32_t);
 }
 
 cudaError_t mark(cudaEvent_t *marks, int i, cudaStream_t stream)
@@ -194,8 +214,32 @@ cudaError_t mark(cudaEvent_t *marks, int i, cudaStream_t stream)
     return marks != nullptr ? cudaEventRecord(marks[i], stream) : cudaSuccess;
 }
 
+// P1 with ITEMS per thread: the odd and even instances, each allowed the
+// shared memory of 4096 buckets on first use on a device.
+template <class T, bool FORWARD, int ITEMS>
+cudaError_t launch_p1(const StagedArgs &a, int device, cudaStream_t stream)
+{
+    static bool configured[64] = {false};
+    if (!configured[device]) {
+        const int most = static_cast<int>(p1_smem_bytes<T, ITEMS>(4096));
+        cudaError_t e = cudaSuccess;
+        for (const void *k : {reinterpret_cast<const void *>(staged_bucket_kernel<T, true, FORWARD, ITEMS>),
+                              reinterpret_cast<const void *>(staged_bucket_kernel<T, false, FORWARD, ITEMS>)})
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (e != cudaSuccess) return e;
+        configured[device] = true;
+    }
+    const size_t dyn = p1_smem_bytes<T, ITEMS>(a.num_dst);
+    const unsigned chunks = static_cast<unsigned>(static_cast<uint64_t>(a.g.n) / (uint64_t{kP1Block} * ITEMS));
+    if (a.g.k & 1u)
+        staged_bucket_kernel<T, true, FORWARD, ITEMS><<<chunks, kP1Block, dyn, stream>>>(a);
+    else
+        staged_bucket_kernel<T, false, FORWARD, ITEMS><<<chunks, kP1Block, dyn, stream>>>(a);
+    return cudaGetLastError();
+}
+
 template <class T, bool FORWARD>
-cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *marks)
+cudaError_t launch_typed(const StagedArgs &a, uint32_t items, cudaStream_t stream, cudaEvent_t *marks)
 {
     static bool configured[64] = {false};
     int device = 0;
@@ -203,28 +247,18 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     if (!configured[device]) {
-        e = cudaFuncSetAttribute(staged_bucket_kernel<T, true, FORWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(p1_smem_bytes<T>(4096)));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(staged_bucket_kernel<T, false, FORWARD>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(p1_smem_bytes<T>(4096)));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(staged_scatter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(kScatterSmemReserve));
+        e = cudaFuncSetAttribute(staged_scatter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kScatterSmemReserve));
         if (e != cudaSuccess) return e;
         configured[device] = true;
     }
-    const size_t dyn = p1_smem_bytes<T>(a.num_dst);
     const unsigned chunks = static_cast<unsigned>(static_cast<uint64_t>(a.g.n) / kSTile);
-    const unsigned p1_chunks = static_cast<unsigned>(static_cast<uint64_t>(a.g.n) / kP1Tile);
     e = mark(marks, 0, stream);
     if (e != cudaSuccess) return e;
-    if (a.g.k & 1u)
-        staged_bucket_kernel<T, true, FORWARD><<<p1_chunks, kP1Block, dyn, stream>>>(a);
+    if constexpr (sizeof(T) <= 8)
+        e = items == 16 ? launch_p1<T, FORWARD, 16>(a, device, stream) : launch_p1<T, FORWARD, 8>(a, device, stream);
     else
-        staged_bucket_kernel<T, false, FORWARD><<<p1_chunks, kP1Block, dyn, stream>>>(a);
-    e = cudaGetLastError();
+        e = launch_p1<T, FORWARD, 8>(a, device, stream);
     if (e == cudaSuccess) e = mark(marks, 1, stream);
     if (e != cudaSuccess) return e;
     staged_scatter_kernel<T><<<chunks, kSBlock, kScatterSmemReserve, stream>>>(a);
@@ -237,18 +271,39 @@ cudaError_t launch_typed(const StagedArgs &a, cudaStream_t stream, cudaEvent_t *
 
 uint32_t staged_tile_size() { return kStagedMinChunk; }
 
+uint32_t staged_window_shift(uint64_t n, uint32_t elem_bytes)
+{
+    uint32_t lg = 0;
+    while ((uint64_t{1} << lg) < n) ++lg;
+    uint32_t eb_log2 = 0;
+    while ((1u << eb_log2) < elem_bytes) ++eb_log2;
+    // one bucket per 8 elements of a P1 chunk: 256 (or 512) buckets
+    uint32_t bucket_log2 = 0;
+    while ((8u << bucket_log2) < static_cast<uint32_t>(kP1Block) * p1_items_for(n, elem_bytes)) ++bucket_log2;
+    uint32_t shift = lg > bucket_log2 ? lg - bucket_log2 : 0u;
+    const uint32_t min_shift = kMinWindowLog2 > eb_log2 ? kMinWindowLog2 - eb_log2 : 0u;
+    if (shift < min_shift) shift = min_shift;
+    if (lg > 12 && shift < lg - 12) shift = lg - 12;  // at most 4096 buckets
+    if (shift > lg) shift = lg;
+    return shift;
+}
+
 cudaError_t launch_staged(const StagedArgs &a, uint32_t elem_bytes, bool inverse, cudaStream_t stream,
                           cudaEvent_t *marks)
 {
+    const uint32_t items = p1_items_for(a.g.n, elem_bytes);
+    const uint64_t p1_tile = items == 16 ? kP1TileLarge : kP1TileSmall;
     if (a.num_dst > 4096 || static_cast<uint64_t>(a.g.n) != a.g.domain || a.g.domain < 2 * kStagedMinChunk ||
-        a.g.domain > (uint64_t{1} << 31) || (uint64_t{1} << a.dst_shift) < kStagedMinChunk)
+        a.g.domain > (uint64_t{1} << 31) || a.g.domain % p1_tile != 0 || (uint64_t{1} << a.dst_shift) < p1_tile ||
+        (uint64_t{1} << a.dst_shift) < kSTile)
         return cudaErrorInvalidValue;
     switch (elem_bytes) {
-    case 4: return inverse ? launch_typed<unsigned int, true>(a, stream, marks)
-                           : launch_typed<unsigned int, false>(a, stream, marks);
-    case 8: return inverse ? launch_typed<unsigned long long, true>(a, stream, marks)
-                           : launch_typed<unsigned long long, false>(a, stream, marks);
-    case 16: return inverse ? launch_typed<uint4, true>(a, stream, marks) : launch_typed<uint4, false>(a, stream, marks);
+    case 4: return inverse ? launch_typed<unsigned int, true>(a, items, stream, marks)
+                           : launch_typed<unsigned int, false>(a, items, stream, marks);
+    case 8: return inverse ? launch_typed<unsigned long long, true>(a, items, stream, marks)
+                           : launch_typed<unsigned long long, false>(a, items, stream, marks);
+    case 16: return inverse ? launch_typed<uint4, true>(a, items, stream, marks)
+                            : launch_typed<uint4, false>(a, items, stream, marks);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -134,3 +134,43 @@ def test_staged_inverse_full_size_round_trip(bs):
     z = bs.permute(y, seed)
     assert_no_device_error()
     assert torch.equal(z, xd)
+
+
+@pytest.mark.parametrize("n,width,rounds", [(2**29, 8, 24), (2**30, 4, 24), (2**29, 4, 20), (2**28, 16, 24)])
+def test_staged_inputs_over_2gib(bs, n, width, rounds):
+    # Inputs over 2 GiB of 4- and 8-byte elements bucket 4,096-element chunks
+    # into up to 512 windows; 16-byte elements keep 2,048-element chunks with
+    # windows over 8 MiB.  x[i] = i, so slot j must hold f(j) (n = 2^k).
+    k, seed = n.bit_length() - 1, 21
+    dtype = {4: torch.int32, 8: torch.int64, 16: torch.int64}[width]
+    xd = torch.arange(n, dtype=dtype, device="cuda")
+    if width == 16:
+        xd = torch.stack([xd, ~xd], dim=1).contiguous()
+    outs = []
+    for strategy in (bs.BSHUFFLE_STRATEGY_STAGED, bs.BSHUFFLE_STRATEGY_PIPELINED):
+        bs.bshuffle_set_strategy(strategy)
+        try:
+            outs.append(bs.permute(xd, seed, rounds))
+            assert_no_device_error()
+        finally:
+            bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
+    assert torch.equal(outs[0], outs[1])
+    js = np.concatenate([np.arange(4096), np.random.default_rng(k).integers(0, n, 100_000),
+                         np.arange(n - 4096, n)]).astype(np.uint64)
+    want = oracle.varphilox(js, k, oracle.round_keys(seed, rounds)).astype(np.int64)
+    got = outs[0][torch.from_numpy(js.astype(np.int64)).cuda()].cpu().numpy()
+    if width == 16:
+        assert np.array_equal(got[:, 0], want) and np.array_equal(got[:, 1], ~want)
+    else:
+        assert np.array_equal(got.astype(np.int64), want)
+    del outs
+    if width != 16:
+        # the inverse shuffle over the same chunking undoes the shuffle
+        bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_STAGED)
+        try:
+            y = bs.permute(xd, seed, rounds)
+            z = bs.inverse(y, seed, rounds)
+            assert_no_device_error()
+        finally:
+            bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
+        assert torch.equal(z, xd)
