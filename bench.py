@@ -64,6 +64,8 @@ def parse():
                    help="only run warmup + steps batched launches over this many instances (for ncu)")
     p.add_argument("--profile-n", type=int, default=0,
                    help="only run warmup + steps launches of the uint64 shuffle at this n (for ncu)")
+    p.add_argument("--table1", action="store_true",
+                   help="only print the Table 1 layout: M items/s of 64-bit keys at lengths 2^w + 1")
     return p.parse_args()
 
 
@@ -666,9 +668,56 @@ def profile_batched(args):
     print(json.dumps({"profile_batched": len(sizes), "elements": int(sizes.sum()), "launch_ms": per}))
 
 
+TABLE1_W = (8, 11, 14, 17, 20, 23, 26, 29)
+
+
+def table1(args):
+    """Tables 1 and 2 of Sec. 6 on this GPU: millions of 64-bit keys shuffled
+    per second at the worst-case lengths 2^w + 1, for the random-gather bound
+    (2^w elements: the measurement kernel takes powers of two), the library's
+    default shuffle (pipelined single pass for these lengths), the paper's
+    fused single pass (Bijective2) and the LCG bijection through the same
+    kernel.  Every launch reuses the same buffers, so lengths up to about
+    2^23 stay resident in the 129 MB L2 between launches."""
+    import torch
+    from paper_2106_06161_gb300 import build as bsbuild
+    bsbuild.build()
+    import paper_2106_06161_gb300 as bs
+    bs.load()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    rows = {}
+    for w in TABLE1_W:
+        n = 2**w + 1
+        x = torch.from_numpy(workloads.uniform_u64(n, w).view(np.int64)).cuda()
+        y = torch.empty_like(x)
+        xp, yp = x.data_ptr(), y.data_ptr()
+        reps = max(10, min(2000, 2**26 // n))
+        cases = (
+            ("gather", 2**w, lambda: bs.bshuffle_random_gather(xp, yp, 2**w, ELEM, sptr)),
+            ("varphilox", n, lambda: bs.bshuffle_permute(xp, yp, n, ELEM, w, ROUNDS, sptr)),
+            ("varphilox_bijective2", n, lambda: bs.bshuffle_permute_ablation(xp, yp, n, ELEM, w, ROUNDS, 2, sptr)),
+            ("lcg", n, lambda: bs.bshuffle_permute_lcg(xp, yp, n, ELEM, w, sptr)),
+        )
+        row = {"reps": reps}
+        for name, items, fn in cases:
+            for _ in range(max(3, args.warmup)):
+                fn()
+            _, region = timed_launches(fn, reps, stream, torch)
+            row[name] = items * reps / (region * 1e-3) / 1e6
+        if bs.get_error() != 0:
+            raise SystemExit("device error")
+        rows[f"2^{w}+1"] = row
+        del x, y
+    print(json.dumps({"table": "M items/s, 64-bit keys, lengths 2^w + 1, 24 rounds, mean over reps launches",
+                      "gpu": torch.cuda.get_device_name(), "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
-    if args.profile_batched:
+    if args.table1:
+        table1(args)
+    elif args.profile_batched:
         profile_batched(args)
     elif args.profile_n:
         profile_case(args)

@@ -303,8 +303,10 @@ int bshuffle_release_workspaces(void);
  *       pass.
  *   BSHUFFLE_STRATEGY_AUTO (default)  staged when it applies and
  *       n * elem_bytes >= 256 MiB; otherwise the pipelined single pass where
- *       it applies, else the plain one; if the staged workspace cannot be
- *       allocated the single pass runs instead.
+ *       it applies and the domain has at least 2^18 indices (2^19 for the
+ *       scatter of bshuffle_inverse), else the plain one (on smaller domains
+ *       a launch is all latency and the plain kernel finishes first); if the
+ *       staged workspace cannot be allocated the single pass runs instead.
  * The setting is process-wide.  Returns BSHUFFLE_ERR_INVALID for other values.
  */
 #define BSHUFFLE_STRATEGY_AUTO 0

@@ -31,6 +31,15 @@ std::atomic<int> g_strategy{BSHUFFLE_STRATEGY_AUTO};
 std::atomic<int> g_pass_timing{0};
 // Auto strategy: the staged path from this many input bytes on.
 constexpr uint64_t kStagedMinBytes = uint64_t{1} << 28;
+// Auto strategy: the pipelined single pass from these domain exponents on.
+// On smaller domains a launch is all latency, and the plain kernel, without
+// the hand-offs between compute warps and look-back warp, finishes first:
+// back-to-back calls at n = 2^m + 1 (4, 8 and 16-byte elements, GB300) took
+// ~8.2 us plain against ~10.2 us pipelined up to m = 14, and the pipelined
+// kernel first won at a 2^18 domain for gathers and indices and at 2^19 for
+// the scatter of bshuffle_inverse.
+constexpr uint32_t kPipeMinKGather = 18;
+constexpr uint32_t kPipeMinKScatter = 19;
 
 // ------------------------------------------------------------------ host math
 
@@ -221,13 +230,15 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     a.timeout_ns = g_timeout_ns.load();
     fill_keys(seed, rounds, a.keys);
     const bool rows = (mode == Mode::Gather || mode == Mode::Scatter) && elem_bytes > 16;
-    // the pipelined kernel: on request and by default, for every call it
-    // serves (it measured faster than the plain kernel for each of them)
+    // the pipelined kernel: on request for every call it serves, and by
+    // default for those over domains of at least 2^18 (2^19 for the scatter)
     const int strategy = g_strategy.load();
+    const bool pipe_by_default = a.g.k >= (mode == Mode::Scatter ? kPipeMinKScatter : kPipeMinKGather);
     const bool pipe = !rows && bsh::pipe_supports(mode, elem_bytes) &&
                       (which == FusedKernel::Pipelined ||
                        (which == FusedKernel::ByStrategy &&
-                        (strategy == BSHUFFLE_STRATEGY_PIPELINED || strategy == BSHUFFLE_STRATEGY_AUTO)));
+                        (strategy == BSHUFFLE_STRATEGY_PIPELINED ||
+                         (strategy == BSHUFFLE_STRATEGY_AUTO && pipe_by_default))));
     const int config = rows ? 0 : bsh::elem_config_for(elem_bytes, mode, rounds);
     const uint64_t tile = rows ? bsh::rows_tile_size(elem_bytes) : (pipe ? bsh::pipe_tile_size(elem_bytes) : bsh::elem_tile_size(config));
     const uint64_t tiles = (a.g.domain + tile - 1) / tile;
