@@ -302,11 +302,14 @@ int bshuffle_release_workspaces(void);
  *       with the look-back.  Same memory traffic and workspace as the single
  *       pass.
  *   BSHUFFLE_STRATEGY_AUTO (default)  staged when it applies and
- *       n * elem_bytes >= 256 MiB; otherwise the pipelined single pass where
- *       it applies and the domain has at least 2^18 indices (2^19 for the
- *       scatter of bshuffle_inverse), else the plain one (on smaller domains
- *       a launch is all latency and the plain kernel finishes first); if the
- *       staged workspace cannot be allocated the single pass runs instead.
+ *       n * elem_bytes >= 256 MiB; otherwise, for n = 2^k >= 16, one launch
+ *       without the scan (nothing is dropped, so the i-th domain index is
+ *       the i-th kept one: out[i] = in[f(i)], out[f(i)] = in[i] or
+ *       out[i] = f(i)); otherwise the pipelined single pass where it applies
+ *       and the domain has at least 2^18 indices (2^19 for the scatter of
+ *       bshuffle_inverse), else the plain one (on smaller domains a launch
+ *       is all latency and the plain kernel finishes first).  If the staged
+ *       workspace cannot be allocated, the scan-free launch runs instead.
  * The setting is process-wide.  Returns BSHUFFLE_ERR_INVALID for other values.
  */
 #define BSHUFFLE_STRATEGY_AUTO 0

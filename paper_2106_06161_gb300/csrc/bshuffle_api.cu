@@ -230,9 +230,29 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     a.timeout_ns = g_timeout_ns.load();
     fill_keys(seed, rounds, a.keys);
     const bool rows = (mode == Mode::Gather || mode == Mode::Scatter) && elem_bytes > 16;
+    const int strategy = g_strategy.load();
+    // n = 2^k: nothing is dropped and the scan is the identity, so by default
+    // the scan-free kernels run (same output, no look-back)
+    if (which == FusedKernel::ByStrategy && strategy == BSHUFFLE_STRATEGY_AUTO && a.g.domain == n) {
+        Workspace *ws = nullptr;
+        const int rc = acquire_workspace(stream, 1, &ws);
+        if (rc != BSHUFFLE_OK) return rc;
+        a.ws = ws->header();
+        a.status = ws->status();
+        cudaEvent_t *marks = mode == Mode::Gather ? timing_marks(ws) : nullptr;
+        if (marks != nullptr && cudaEventRecord(marks[0], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+        const cudaError_t e = bsh::launch_direct(a, mode, elem_bytes, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (marks != nullptr) {
+            if (cudaEventRecord(marks[1], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+            ws->marks_recorded = 2;
+        } else if (mode == Mode::Gather) {
+            ws->marks_recorded = 0;
+        }
+        return BSHUFFLE_OK;
+    }
     // the pipelined kernel: on request for every call it serves, and by
     // default for those over domains of at least 2^18 (2^19 for the scatter)
-    const int strategy = g_strategy.load();
     const bool pipe_by_default = a.g.k >= (mode == Mode::Scatter ? kPipeMinKScatter : kPipeMinKGather);
     const bool pipe = !rows && bsh::pipe_supports(mode, elem_bytes) &&
                       (which == FusedKernel::Pipelined ||

@@ -91,6 +91,10 @@ cudaError_t launch_gather_tuned(const TileArgs &a, uint32_t elem_bytes, int conf
 // The fused gather with the LCG bijection (default configuration).
 cudaError_t launch_gather_lcg(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream);
 cudaError_t launch_rows(const TileArgs &a, Mode mode, cudaStream_t stream);
+// Power-of-two lengths (g.n == g.domain >= 16): Algorithm 1 without its scan,
+// which is the identity when nothing is dropped.  Every mode; elem_bytes 1,
+// 2, 4, 8, 16 or rows of a multiple of 16 bytes.
+cudaError_t launch_direct(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream);
 
 // ------------------------------------------------------------------ batched
 
