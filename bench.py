@@ -1,22 +1,31 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the GB300 bijective shuffle.
 
-Workload (one "step"): one fused shuffle of n = 2^28 uniform random 64-bit
-keys (the paper's Sec. 6 payload) already resident in HBM: bijection, keep
-flags, in-tile scan, decoupled look-back, gather and compacted store, all in
-one launch of the library's kernel through the C ABI.  Inputs (2 GiB) are far
+Workload (one "step"): one shuffle of n = 2^28 uniform random 64-bit keys
+(the paper's Sec. 6 payload) already resident in HBM, through the C ABI with
+the library's default strategy.  For this power-of-two length that is the
+staged path: pass 1 reads the keys in order, inverts the bijection and
+buckets (key, slot) by output window; pass 2 scatters each window while it
+sits in L2 (same output as Algorithm 1's fused single pass, which
+--strategy single_pass or pipelined times instead).  Inputs (2 GiB) are far
 larger than the 129 MB L2, so no flush is needed between steps.
 
 Printed on one JSON line (rank 0):
   value        shuffled elements per second, whole job (all ranks)
-  roofline     algorithmic bytes 2 * n * 8 per launch over the measured launch
-               time, against the measured HBM copy peak
+  roofline     the dominant kernel of the step: its algorithmic bytes per
+               launch over its CUDA-event launch time, against the measured
+               HBM copy peak, with its DRAM traffic from the committed ncu
+               record while the kernel source is unchanged
   e2e          the same metric through the C ABI from pinned host buffers,
                host-to-device and device-to-host copies inside the timed region
   cpu_baseline the CPU oracle, as it stands, on a bounded sample of the same
                workload (the first slots of the same shuffle)
-  extra        worst-case padding (n = 2^28 + 12345) and the 4096-instance
-               uneven batch, batched launch vs one plain launch per instance
+  extra        every strategy at n = 2^28 and at the worst-case padding
+               n = 2^28 + 12345, the inverse and index outputs, the Sec. 6
+               fusion ablation, the Sec. 5 round-count study, the random
+               gather bound, the autograd row shuffle, the Monte Carlo and
+               Shapley consumers, and the 4096-instance uneven batch
+               (batched launch vs one plain launch per instance)
 
 `--impl reference` times the CPU oracle on this workload instead (bounded
 sample per step) and prints the same line with "impl": "reference".
