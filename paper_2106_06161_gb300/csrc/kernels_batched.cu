@@ -13,6 +13,7 @@
 // A small planning kernel (one CTA) runs first: it validates the descriptors,
 // computes every instance's domain exponent and tile count, scans the tile
 // counts, and clears the status ring used by the look-back.
+#include <atomic>
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -533,12 +534,13 @@ cudaError_t launch_pipe_typed(const BatchArgs &a, cudaStream_t stream)
 {
     constexpr int THREADS = (kPipeWarps + 1) * 32;
     constexpr size_t DYN = 2 * sizeof(T) * kTile;
-    static int per_sm[64] = {0};
+    static std::atomic<int> per_sm[64];  // CTAs to launch per device, 0 until first use
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (per_sm[device] == 0) {
+    int ctas_cached = per_sm[device].load(std::memory_order_acquire);
+    if (ctas_cached == 0) {
         e = cudaFuncSetAttribute(batch_pipe_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(DYN));
         if (e != cudaSuccess) return e;
         int blocks = 0, sms = 0;
@@ -546,10 +548,11 @@ cudaError_t launch_pipe_typed(const BatchArgs &a, cudaStream_t stream)
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
-        per_sm[device] = (blocks > 0 ? blocks : 1) * sms;
+        ctas_cached = (blocks > 0 ? blocks : 1) * sms;
+        per_sm[device].store(ctas_cached, std::memory_order_release);
     }
     BatchArgs b = a;
-    b.grid = static_cast<uint32_t>(per_sm[device]);
+    b.grid = static_cast<uint32_t>(ctas_cached);
     batch_plan_kernel<<<1, kPlanThreads, 0, stream>>>(b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -560,21 +563,23 @@ cudaError_t launch_pipe_typed(const BatchArgs &a, cudaStream_t stream)
 template <class T>
 cudaError_t launch_typed(const BatchArgs &a, cudaStream_t stream)
 {
-    static int per_sm[64] = {0};
+    static std::atomic<int> per_sm[64];  // CTAs to launch per device, 0 until first use
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (per_sm[device] == 0) {
+    int ctas_cached = per_sm[device].load(std::memory_order_acquire);
+    if (ctas_cached == 0) {
         int blocks = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_tile_kernel<T>, kBBlock, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
-        per_sm[device] = (blocks > 0 ? blocks : 1) * sms;
+        ctas_cached = (blocks > 0 ? blocks : 1) * sms;
+        per_sm[device].store(ctas_cached, std::memory_order_release);
     }
     BatchArgs b = a;
-    b.grid = static_cast<uint32_t>(per_sm[device]);
+    b.grid = static_cast<uint32_t>(ctas_cached);
     batch_plan_kernel<<<1, kPlanThreads, 0, stream>>>(b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

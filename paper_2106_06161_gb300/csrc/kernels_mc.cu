@@ -11,6 +11,7 @@
 // are kept every later kept element belongs to the second group, whose sum
 // is the total minus the first group's: the walk stops there.  The total is
 // summed once per CTA, in the same order in every CTA.
+#include <atomic>
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -100,21 +101,23 @@ __global__ void __launch_bounds__(kMcBlock) mc_kernel(const __grid_constant__ Mc
 
 cudaError_t launch_mc(const McArgs &a, cudaStream_t stream)
 {
-    static int per_sm[64] = {0};
+    static std::atomic<int> per_sm[64];  // CTAs to launch per device, 0 until first use
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (per_sm[device] == 0) {
+    int ctas_cached = per_sm[device].load(std::memory_order_acquire);
+    if (ctas_cached == 0) {
         int blocks = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mc_kernel<true>, kMcBlock, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
-        per_sm[device] = (blocks > 0 ? blocks : 1) * sms;
+        ctas_cached = (blocks > 0 ? blocks : 1) * sms;
+        per_sm[device].store(ctas_cached, std::memory_order_release);
     }
     const uint32_t want = (a.count + kMcWarps - 1) / kMcWarps;  // one warp per instance
-    const uint32_t grid = want < static_cast<uint32_t>(per_sm[device]) ? want : per_sm[device];
+    const uint32_t grid = want < static_cast<uint32_t>(ctas_cached) ? want : ctas_cached;
     if (a.g.k & 1u)
         mc_kernel<true><<<grid, kMcBlock, 0, stream>>>(a);
     else

@@ -25,6 +25,7 @@
 // look-back, and the compute warps wait for a rank only after that.  The
 // smallest unfinished ticket therefore always makes progress.  Every wait is
 // bounded.
+#include <atomic>
 #include <cstdint>
 #include <type_traits>
 
@@ -267,14 +268,15 @@ cudaError_t launch_typed(const TileArgs &a, cudaStream_t stream)
     constexpr int NCW = kPipeComputeWarps, ITEMS = pipe_items(sizeof(T));
     constexpr int THREADS = (NCW + 1) * 32;
     constexpr size_t DYN = sizeof(PipeSlot<T, MODE>) * 2 * pipe_tile(sizeof(T));
-    static int per_sm[64][2] = {};
+    static std::atomic<int> per_sm[64][2];  // CTAs to launch per device and parity, 0 until first use
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     const bool odd = (a.g.k & 1u) != 0u;
     auto kernel = odd ? pipe_tile_kernel<T, MODE, true, NCW, ITEMS> : pipe_tile_kernel<T, MODE, false, NCW, ITEMS>;
-    int &ctas = per_sm[device][odd ? 1 : 0];
+    std::atomic<int> &slot = per_sm[device][odd ? 1 : 0];
+    int ctas = slot.load(std::memory_order_acquire);
     if (ctas == 0) {
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(DYN));
         if (e != cudaSuccess) return e;
@@ -284,6 +286,7 @@ cudaError_t launch_typed(const TileArgs &a, cudaStream_t stream)
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
         ctas = (blocks > 0 ? blocks : 1) * sms;
+        slot.store(ctas, std::memory_order_release);
     }
     const uint32_t grid = a.num_tiles < static_cast<uint32_t>(ctas) ? a.num_tiles : static_cast<uint32_t>(ctas);
     kernel<<<grid, THREADS, DYN, stream>>>(a);

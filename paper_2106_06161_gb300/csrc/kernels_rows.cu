@@ -11,6 +11,7 @@
 // (a 4 KiB row per warp step), so that enough bytes are in flight per SM to
 // cover the HBM latency: with 256 rows per tile a [65536 x 1024] FP32
 // shuffle had fewer than two CTAs per SM and was latency-bound.
+#include <atomic>
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -118,21 +119,23 @@ uint32_t rows_tile_size(uint32_t row_bytes) { return rows_per_tile(row_bytes); }
 template <int ROWS>
 cudaError_t launch_rows_t(const TileArgs &a, Mode mode, cudaStream_t stream)
 {
-    static int per_sm[64] = {0};
+    static std::atomic<int> per_sm[64];  // CTAs to launch per device, 0 until first use
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (per_sm[device] == 0) {
+    int ctas_cached = per_sm[device].load(std::memory_order_acquire);
+    if (ctas_cached == 0) {
         int blocks = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, rows_tile_kernel<Mode::Gather, true, ROWS>,
                                                           kRowBlock, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
-        per_sm[device] = (blocks > 0 ? blocks : 1) * sms;
+        ctas_cached = (blocks > 0 ? blocks : 1) * sms;
+        per_sm[device].store(ctas_cached, std::memory_order_release);
     }
-    const uint32_t ctas = a.num_tiles < static_cast<uint32_t>(per_sm[device]) ? a.num_tiles : per_sm[device];
+    const uint32_t ctas = a.num_tiles < static_cast<uint32_t>(ctas_cached) ? a.num_tiles : ctas_cached;
     const dim3 grid(ctas), block(kRowBlock);
     const bool odd = (a.g.k & 1u) != 0u;
     if (mode == Mode::Gather) {

@@ -11,6 +11,7 @@
 // running weight with warp scans plus a carry (no block barrier, no
 // inter-warp communication), and stops once the total reaches q.  The order
 // itself never leaves registers.
+#include <atomic>
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -70,20 +71,22 @@ __global__ void __launch_bounds__(kSvBlock) shapley_voting_kernel(const __grid_c
 
 cudaError_t launch_shapley_voting(const ShapleyArgs &a, cudaStream_t stream)
 {
-    static int per_sm[64] = {0};
+    static std::atomic<int> per_sm[64];  // CTAs to launch per device, 0 until first use
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (per_sm[device] == 0) {
+    int ctas_cached = per_sm[device].load(std::memory_order_acquire);
+    if (ctas_cached == 0) {
         int blocks = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, shapley_voting_kernel<true>, kSvBlock, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
-        per_sm[device] = (blocks > 0 ? blocks : 1) * sms;
+        ctas_cached = (blocks > 0 ? blocks : 1) * sms;
+        per_sm[device].store(ctas_cached, std::memory_order_release);
     }
-    const uint64_t cap = static_cast<uint64_t>(per_sm[device]);
+    const uint64_t cap = static_cast<uint64_t>(ctas_cached);
     const uint64_t want = (a.samples + kSvWarps - 1) / kSvWarps;  // one warp per sample
     const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
     if (a.g.k & 1u)

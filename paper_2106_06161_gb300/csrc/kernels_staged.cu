@@ -32,6 +32,7 @@
 // one per 8 elements of a P1 chunk, and inputs over 2 GiB of 4- or 8-byte
 // elements use 4,096-element chunks (16 items per thread), which halves the
 // appends per element and allows 512 buckets.
+#include <atomic>
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -219,15 +220,15 @@ cudaError_t mark(cudaEvent_t *marks, int i, cudaStream_t stream)
 template <class T, bool FORWARD, int ITEMS>
 cudaError_t launch_p1(const StagedArgs &a, int device, cudaStream_t stream)
 {
-    static bool configured[64] = {false};
-    if (!configured[device]) {
+    static std::atomic<bool> configured[64];  // attribute set on this device
+    if (!configured[device].load(std::memory_order_acquire)) {
         const int most = static_cast<int>(p1_smem_bytes<T, ITEMS>(4096));
         cudaError_t e = cudaSuccess;
         for (const void *k : {reinterpret_cast<const void *>(staged_bucket_kernel<T, true, FORWARD, ITEMS>),
                               reinterpret_cast<const void *>(staged_bucket_kernel<T, false, FORWARD, ITEMS>)})
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (e != cudaSuccess) return e;
-        configured[device] = true;
+        configured[device].store(true, std::memory_order_release);
     }
     const size_t dyn = p1_smem_bytes<T, ITEMS>(a.num_dst);
     const unsigned chunks = static_cast<unsigned>(static_cast<uint64_t>(a.g.n) / (uint64_t{kP1Block} * ITEMS));
@@ -241,16 +242,16 @@ cudaError_t launch_p1(const StagedArgs &a, int device, cudaStream_t stream)
 template <class T, bool FORWARD>
 cudaError_t launch_typed(const StagedArgs &a, uint32_t items, cudaStream_t stream, cudaEvent_t *marks)
 {
-    static bool configured[64] = {false};
+    static std::atomic<bool> configured[64];  // attribute set on this device
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (!configured[device]) {
+    if (!configured[device].load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(staged_scatter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(kScatterSmemReserve));
         if (e != cudaSuccess) return e;
-        configured[device] = true;
+        configured[device].store(true, std::memory_order_release);
     }
     const unsigned chunks = static_cast<unsigned>(static_cast<uint64_t>(a.g.n) / kSTile);
     e = mark(marks, 0, stream);
