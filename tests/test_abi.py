@@ -135,3 +135,38 @@ def test_shapley_argument_errors(lib):
     assert f(a, 8, 5, 0, 10, 24, a + 260, None) == L.BSHUFFLE_ERR_ALIGN
     assert f(a, 2**32, 5, 0, 10, 24, a + 256, None) == L.BSHUFFLE_ERR_TOO_LARGE
     assert f(None, 0, 5, 0, 10, 24, None, None) == L.BSHUFFLE_OK
+
+
+def test_every_launch_path_fails_loudly_without_a_device(lib):
+    # Lengths that take the scan-free launch (n = 2^k), the fused single pass
+    # (other n) and the allocation-free entry point: without a device each
+    # returns BSHUFFLE_ERR_CUDA, never a host-side result.
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2106_06161_gb300 import _lib as L
+    buf = (ctypes.c_uint64 * 64)()
+    a = ctypes.addressof(buf)
+    for n, elem in ((16, 8), (5, 8), (32, 4), (4, 32)):
+        assert lib.bshuffle_permute(a, a + 256, n, elem, 0, 24, None) == L.BSHUFFLE_ERR_CUDA, (n, elem)
+        assert lib.bshuffle_inverse(a, a + 256, n, elem, 0, 24, None) == L.BSHUFFLE_ERR_CUDA, (n, elem)
+    for n in (16, 17):
+        assert lib.bshuffle_indices(a, 8, n, 0, 24, None) == L.BSHUFFLE_ERR_CUDA
+    assert lib.bshuffle_permute_static(a, a + 256, 16, 8, 0, 24, None) == L.BSHUFFLE_ERR_CUDA
+    assert buf[:] == [0] * 64  # nothing was written on the host
+
+
+def test_allocation_free_entry_point_argument_errors(lib):
+    # size and width limits of the fixed scratch array are checked before
+    # any CUDA call
+    from paper_2106_06161_gb300 import _lib as L
+    buf = (ctypes.c_uint64 * 64)()
+    a = ctypes.addressof(buf)
+    f = lib.bshuffle_permute_static
+    assert f(a, a + 256, 2**27 + 1, 1, 0, 24, None) == L.BSHUFFLE_ERR_TOO_LARGE
+    assert f(a, a + 256, 4, 32, 0, 24, None) == L.BSHUFFLE_ERR_ELEM
+    assert f(a, a + 256, 4, 3, 0, 24, None) == L.BSHUFFLE_ERR_ELEM
+    assert f(a, a + 256, 4, 8, 0, 65, None) == L.BSHUFFLE_ERR_ROUNDS
+    assert f(a, a + 16, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_ALIAS
+    assert f(a + 4, a + 256, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_ALIGN
+    assert f(a, a + 256, 0, 8, 0, 24, None) == L.BSHUFFLE_OK
