@@ -15,11 +15,13 @@
  * call: the bijection in registers, the compaction as an in-tile scan chained
  * across tiles by decoupled look-back (single pass, Sec. 4 last paragraph and
  * the "Bijective2" variant of Sec. 6), the gather of each kept element once,
- * and a coalesced store into its compacted slot.  By default the single pass
- * runs pipelined (a dedicated warp per CTA does the look-back while the other
- * warps evaluate the next tile), and inputs much larger than L2 of
- * power-of-two length run a staged two-pass variant; the output is the same
- * (see bshuffle_set_strategy).
+ * and a coalesced store into its compacted slot.  By default the library
+ * picks among variants with the same output (see bshuffle_set_strategy):
+ * inputs much larger than L2 of power-of-two length run a staged two-pass
+ * variant; other power-of-two lengths run one launch without the scan (with
+ * nothing dropped, slot j holds X[f(j)]); other lengths run the single pass,
+ * pipelined on large domains (a dedicated warp per CTA does the look-back
+ * while the other warps evaluate the next tile).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -103,7 +105,7 @@ typedef struct bshuffle_desc {
  *   elem_bytes  1, 2, 4, 8 or a multiple of 16
  *   seed        key seed; rounds: cipher rounds (24 recommended)
  *   stream      cudaStream_t as void*
- * Returns BSHUFFLE_OK once the kernel is enqueued.
+ * Returns BSHUFFLE_OK once the kernels are enqueued.
  */
 int bshuffle_permute(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                      uint32_t rounds, void *stream);
