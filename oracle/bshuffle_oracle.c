@@ -11,8 +11,7 @@
  * Everything here is written for obviousness, not speed: one index at a
  * time, in the order the paper states the algorithm.
  *
- * Readings of the paper taken here (each is also listed with its reason in
- * the design notes of the repository):
+ * Readings of the paper taken here, each with its reason:
  *   R1  mulhilo is the full 64-bit product of the 64-bit constant M0 with
  *       the zero-extended 32-bit left half, reduced mod 2^64, then split into
  *       upper and lower 32-bit words (Sec. 3.2, Listing 1 and its caption).
