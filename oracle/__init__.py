@@ -6,7 +6,9 @@ with the CUDA library in ``paper_2106_06161_gb300`` and never calls it; the
 product path must not import it.
 
 The arithmetic lives in ``bshuffle_oracle.c`` (plain sequential C, built with
-gcc on first use).  This module only marshals numpy arrays in and out.  The
+gcc on first use; the ``*_mt`` functions run Algorithm 1 on several host
+threads over consecutive domain ranges: count, exclusive scan, write).  This
+module only marshals numpy arrays in and out.  The
 statistical tests of Sec. 5 are in :mod:`oracle.stats`.
 """
 from __future__ import annotations
@@ -37,7 +39,7 @@ def build(force: bool = False) -> str:
              or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-pthread", "-shared", "-fPIC",
                                "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -64,6 +66,10 @@ def _load():
             "oracle_permute": (u64, [p, p, u64, u32, u64, u32]),
             "oracle_permute_first": (u64, [p, p, u64, u32, u64, u32, u64]),
             "oracle_inverse": (u64, [p, p, u64, u32, u64, u32]),
+            "oracle_count_range": (u64, [u64, u64, u32, u64, u64]),
+            "oracle_default_threads": (u32, []),
+            "oracle_indices_mt": (u64, [p, u64, u64, u32, u32]),
+            "oracle_permute_mt": (u64, [p, p, u64, u32, u64, u32, u32]),
             "oracle_sample_permutations": (None, [p, u32, u64, u64, u32]),
             "oracle_fisher_yates": (None, [p, u64, u32, u64]),
             "oracle_mc_statistics": (None, [p, u64, u64, u64, u64, u32, p]),
@@ -182,6 +188,42 @@ def inverse(y: np.ndarray, seed: int, rounds: int = DEFAULT_ROUNDS) -> np.ndarra
     got = _load().oracle_inverse(_ptr(y), _ptr(out), n, elem_bytes, seed & (2**64 - 1), rounds)
     if got != n:
         raise ValueError("inverse kept a wrong count")
+    return out
+
+
+def count_range(n: int, seed: int, i0: int, i1: int, rounds: int = DEFAULT_ROUNDS) -> int:
+    """Kept domain indices in [i0, i1) of the shuffle of length n: the range's
+    share of Algorithm 1's exclusive scan."""
+    return int(_load().oracle_count_range(n, seed & (2**64 - 1), rounds, i0, i1))
+
+
+def default_threads() -> int:
+    """Host threads the threaded functions use when given threads=0."""
+    return int(_load().oracle_default_threads())
+
+
+def indices_mt(n: int, seed: int, rounds: int = DEFAULT_ROUNDS, threads: int = 0) -> np.ndarray:
+    """:func:`indices` computed by `threads` host threads over consecutive
+    domain ranges (count, exclusive scan of the counts, write); same output."""
+    idx = np.zeros(max(n, 1), dtype=np.uint64)
+    if n == 0:
+        return idx[:0]
+    got = _load().oracle_indices_mt(_ptr(idx), n, seed & (2**64 - 1), rounds, threads)
+    if got != n:
+        raise ValueError(f"threaded indices kept {got} of {n}")
+    return idx
+
+
+def permute_mt(x: np.ndarray, seed: int, rounds: int = DEFAULT_ROUNDS, threads: int = 0) -> np.ndarray:
+    """:func:`permute` computed by `threads` host threads (count, scan, gather)."""
+    x = np.ascontiguousarray(x)
+    n = x.shape[0]
+    out = np.empty_like(x)
+    if n == 0:
+        return out
+    got = _load().oracle_permute_mt(_ptr(x), _ptr(out), n, x.nbytes // n, seed & (2**64 - 1), rounds, threads)
+    if got != n:
+        raise ValueError(f"threaded permute kept {got} of {n}")
     return out
 
 

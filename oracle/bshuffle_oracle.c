@@ -9,7 +9,12 @@
  * CUDA path never calls it.
  *
  * Everything here is written for obviousness, not speed: one index at a
- * time, in the order the paper states the algorithm.
+ * time, in the order the paper states the algorithm.  The *_mt functions run
+ * the same loop on several host threads over consecutive ranges of the
+ * domain (a count per range, the exclusive scan of the counts in range
+ * order, then a write per range from its scanned offset); they are the
+ * multi-core CPU baseline and check large outputs in full, and the
+ * test-suite pins them to brute force.
  *
  * Readings of the paper taken here, each with its reason:
  *   R1  mulhilo is the full 64-bit product of the 64-bit constant M0 with
@@ -39,9 +44,12 @@
  * n = 5 fails below 20 rounds and passes at 24), which the 32 x 32-bit
  * reading of "mulhilo" would not reproduce.
  */
+#define _POSIX_C_SOURCE 200809L  /* sysconf, pthreads */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 /* Philox multiplier named in Listing 1 (Sec. 3.2), from Salmon et al. */
 static const uint64_t ORACLE_M0 = 0xD2B74407B1CE6E93ULL;
@@ -307,6 +315,168 @@ uint64_t oracle_inverse(const void *in, void *out, uint64_t n, uint32_t elem_byt
         }
     }
     return j;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1 over domain ranges: count, exclusive scan, then write     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Number of domain indices i in [i0, i1) whose image f(i) is kept (below n),
+ * on the domain of n.  Summed over a partition of [0, 2^k) into consecutive
+ * ranges, these counts scanned in range order give each range's first output
+ * slot: Algorithm 1's exclusive scan taken at the range boundaries.
+ */
+uint64_t oracle_count_range(uint64_t n, uint64_t seed, uint32_t rounds, uint64_t i0, uint64_t i1)
+{
+    uint32_t keys[256];
+    uint32_t k = oracle_domain_bits(n);
+    uint64_t domain, i, count = 0;
+    if (n == 0 || rounds > 256 || k > 40)
+        return 0;
+    oracle_round_keys(seed, rounds, keys);
+    domain = (uint64_t)1 << k;
+    if (i1 > domain)
+        i1 = domain;
+    for (i = i0; i < i1; i++)
+        if (oracle_varphilox(i, k, keys, rounds) < n)
+            count++;
+    return count;
+}
+
+/*
+ * The same Algorithm 1 run by T host threads, each over one of T consecutive
+ * ranges of the domain: every thread counts its kept indices, the counts are
+ * scanned in range order (exclusive), and every thread then writes its kept
+ * images (or elements) from its scanned offset.  The output equals the
+ * sequential oracle_indices_k / oracle_permute_k; this is the multi-core
+ * count-then-gather form of the method, used as a CPU baseline and to check
+ * large GPU outputs in full.
+ */
+typedef struct {
+    uint64_t lo, hi;            /* domain range [lo, hi) */
+    uint64_t n;
+    uint32_t k, rounds;
+    const uint32_t *keys;
+    uint64_t count;             /* kept indices in the range (pass 1) */
+    uint64_t offset;            /* first output slot of the range (pass 2) */
+    uint64_t *idx;              /* indices output, or NULL */
+    const unsigned char *in;    /* permute input, or NULL */
+    unsigned char *out;         /* permute output */
+    uint32_t elem_bytes;
+} oracle_range_job;
+
+static void *oracle_range_count(void *arg)
+{
+    oracle_range_job *job = (oracle_range_job *)arg;
+    uint64_t i, count = 0;
+    for (i = job->lo; i < job->hi; i++)
+        if (oracle_varphilox(i, job->k, job->keys, job->rounds) < job->n)
+            count++;
+    job->count = count;
+    return NULL;
+}
+
+static void *oracle_range_write(void *arg)
+{
+    oracle_range_job *job = (oracle_range_job *)arg;
+    uint64_t i, j = job->offset;
+    for (i = job->lo; i < job->hi; i++) {
+        uint64_t b = oracle_varphilox(i, job->k, job->keys, job->rounds);
+        if (b < job->n) {
+            if (job->idx != NULL)
+                job->idx[j] = b;
+            else
+                memcpy(job->out + j * job->elem_bytes, job->in + b * job->elem_bytes, job->elem_bytes);
+            j++;
+        }
+    }
+    return NULL;
+}
+
+/* Runs fn over every job, one thread each (the calling thread takes job 0). */
+static int oracle_run_jobs(void *(*fn)(void *), oracle_range_job *jobs, uint32_t threads)
+{
+    pthread_t tid[256];
+    uint32_t t, started = 0;
+    int rc = 0;
+    for (t = 1; t < threads; t++) {
+        if (pthread_create(&tid[t], NULL, fn, &jobs[t]) != 0) {
+            rc = -1;
+            break;
+        }
+        started = t;
+    }
+    if (rc == 0)
+        fn(&jobs[0]);
+    for (t = 1; t <= started; t++)
+        pthread_join(tid[t], NULL);
+    return rc;
+}
+
+uint32_t oracle_default_threads(void)
+{
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    if (c < 1)
+        return 1;
+    return c > 256 ? 256u : (uint32_t)c;
+}
+
+/* Count, scan, write: the threaded form of Algorithm 1 (idx or in/out). */
+static uint64_t oracle_algorithm1_mt(uint64_t *idx, const void *in, void *out, uint64_t n, uint32_t elem_bytes,
+                                     uint32_t k, uint64_t seed, uint32_t rounds, uint32_t threads)
+{
+    oracle_range_job jobs[256];
+    uint32_t keys[256];
+    uint64_t domain, total = 0;
+    uint32_t t;
+    if (n == 0 || rounds > 256 || k > 40)
+        return 0;
+    if (threads == 0)
+        threads = oracle_default_threads();
+    if (threads > 256)
+        threads = 256;
+    oracle_round_keys(seed, rounds, keys);
+    domain = (uint64_t)1 << k;
+    if (threads > domain)
+        threads = (uint32_t)domain;
+    for (t = 0; t < threads; t++) {
+        memset(&jobs[t], 0, sizeof(jobs[t]));
+        jobs[t].lo = domain / threads * t;
+        jobs[t].hi = t + 1 == threads ? domain : domain / threads * (t + 1);
+        jobs[t].n = n;
+        jobs[t].k = k;
+        jobs[t].rounds = rounds;
+        jobs[t].keys = keys;
+        jobs[t].idx = idx;
+        jobs[t].in = (const unsigned char *)in;
+        jobs[t].out = (unsigned char *)out;
+        jobs[t].elem_bytes = elem_bytes;
+    }
+    if (oracle_run_jobs(oracle_range_count, jobs, threads) != 0)
+        return 0;
+    for (t = 0; t < threads; t++) {   /* exclusive scan of the range counts */
+        jobs[t].offset = total;
+        total += jobs[t].count;
+    }
+    if (total != n)
+        return total;                 /* not a bijection onto [0, n): write nothing */
+    if (oracle_run_jobs(oracle_range_write, jobs, threads) != 0)
+        return 0;
+    return total;
+}
+
+uint64_t oracle_indices_mt(uint64_t *idx, uint64_t n, uint64_t seed, uint32_t rounds, uint32_t threads)
+{
+    return oracle_algorithm1_mt(idx, NULL, NULL, n, 0, oracle_domain_bits(n), seed, rounds, threads);
+}
+
+uint64_t oracle_permute_mt(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                           uint32_t rounds, uint32_t threads)
+{
+    if (in == NULL || out == NULL || elem_bytes == 0)
+        return 0;
+    return oracle_algorithm1_mt(NULL, in, out, n, elem_bytes, oracle_domain_bits(n), seed, rounds, threads);
 }
 
 /* count permutations of length n (as idx arrays, uint32) from seeds

@@ -117,3 +117,41 @@ def test_mc_statistic_closed_forms():
         y = oracle.permute(x, 100 + b).astype(np.float64)
         gap = math.fsum(y[:n1]) / n1 - math.fsum(y[n1:]) / (x.size - n1)
         assert abs(T[b] - gap) <= 1e-12 * max(1.0, abs(gap))
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 8, 0])
+def test_threaded_algorithm_1_matches_brute_force(threads):
+    # count per domain range, exclusive scan of the counts, write per range:
+    # the same output as Algorithm 1 by its definition, for any split
+    for n in (1, 2, 3, 5, 17, 1000, 4097, 65537):
+        for seed in (0, 4):
+            want = _brute_force_indices(n, seed, 24, oracle.domain_bits(n))
+            assert np.array_equal(oracle.indices_mt(n, seed, threads=threads), want), (n, seed)
+    x = workloads.uniform_u64(100_003, 1)
+    want = x[_brute_force_indices(100_003, 6, 24, oracle.domain_bits(100_003)).astype(np.int64)]
+    assert np.array_equal(oracle.permute_mt(x, 6, threads=threads), want)
+    rows = np.random.default_rng(2).integers(0, 256, size=(5000, 48), dtype=np.uint8)
+    want = rows[_brute_force_indices(5000, 7, 24, oracle.domain_bits(5000)).astype(np.int64)]
+    assert np.array_equal(oracle.permute_mt(rows, 7, threads=threads), want)
+
+
+def test_count_range_gives_the_scan_at_range_boundaries():
+    # splitting the domain into consecutive ranges: each range's kept count,
+    # scanned in range order, is the first output slot of the range, and the
+    # slots of the range hold exactly the range's kept images in order
+    n, seed = 3001, 12
+    k = oracle.domain_bits(n)
+    keys = oracle.round_keys(seed, 24)
+    img = oracle.varphilox(np.arange(2**k, dtype=np.uint64), k, keys)
+    idx = oracle.indices(n, seed)
+    bounds = [0, 1, 700, 2048, 2049, 4000, 2**k]
+    start = 0
+    for i0, i1 in zip(bounds[:-1], bounds[1:]):
+        c = oracle.count_range(n, seed, i0, i1)
+        kept = img[i0:i1][img[i0:i1] < n]
+        assert c == kept.size
+        assert np.array_equal(idx[start:start + c], kept)
+        start += c
+    assert start == n
+    assert oracle.count_range(n, seed, 0, 2**40) == n  # clipped to the domain
+    assert oracle.count_range(n, seed, 5, 5) == 0
