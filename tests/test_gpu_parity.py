@@ -1,10 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Everything the library computes is integer index arithmetic and byte moves,
-so the bar is bit-exact equality for every width.  Small and mid sizes are
-compared element by element; the full-size sweep points are compared against
-one full oracle pass (2^28 + 12345) or against the oracle evaluated at sampled
-slots (2^28, no dropped indices), plus properties that hold at any size."""
+so the bar is bit-exact equality for every width, compared element by
+element.  The sweep's full sizes (2^28 and 2^28 + 12345, seeds 0..4) are
+compared slot by slot in test_gpu_full_size.py."""
 import numpy as np
 import pytest
 import torch
@@ -129,89 +128,6 @@ def test_sweep_sizes_up_to_2_24(width):
                 continue
             x = workloads.sweep_payload(n, width, seed)
             assert np.array_equal(gpu_permute(x, seed), oracle.permute(x, seed)), (n, seed)
-
-
-def _window_check(idx: np.ndarray, n: int, seed: int, starts):
-    """Consecutive slots must come from increasing domain indices with every
-    index in between dropped (its image is >= n)."""
-    k = oracle.domain_bits(n)
-    keys = oracle.round_keys(seed, 24)
-    for j0 in starts:
-        win = idx[j0:j0 + 256].astype(np.uint64)
-        pre = oracle.varphilox_inverse(win, k, keys)
-        assert np.all(np.diff(pre.astype(np.int64)) > 0)
-        between = np.setdiff1d(np.arange(int(pre[0]), int(pre[-1]) + 1, dtype=np.uint64), pre)
-        assert np.all(oracle.varphilox(between, k, keys) >= n)
-
-
-def test_full_size_power_of_two_u64_sampled():
-    # n = 2^28 uint64: no index is dropped, so slot j holds X[f(j)].
-    n, seed = 2**28, 0
-    x = workloads.uniform_u64(n, seed)
-    xd = to_device(x)
-    y = bs.permute(xd, seed)
-    assert_no_device_error()
-    rng = np.random.default_rng(1)
-    js = np.concatenate([np.arange(4096), rng.integers(0, n, 200_000), np.arange(n - 4096, n)]).astype(np.uint64)
-    src = oracle.varphilox(js, 28, oracle.round_keys(seed, 24))
-    got = y[torch.from_numpy(js.astype(np.int64)).cuda()].cpu().numpy().view(np.uint64)
-    assert np.array_equal(got, x[src.astype(np.int64)])
-    # any size: the output is a permutation of the input
-    assert torch.equal(torch.sort(y).values, torch.sort(xd).values)
-
-
-@pytest.fixture(scope="module")
-def worst_case_indices():
-    # one oracle pass of the n = 2^28 + 12345 shuffle with seed 0
-    return oracle.indices(2**28 + 12345, 0)
-
-
-def test_full_size_worst_case_padding_exact(worst_case_indices):
-    # n = 2^28 + 12345 (domain 2^29, about half the images dropped): one full
-    # oracle pass, compared slot for slot with the GPU's indices and payload.
-    n, seed = 2**28 + 12345, 0
-    want = worst_case_indices
-    idx = bs.indices(n, seed, dtype=torch.int64)
-    assert_no_device_error()
-    assert np.array_equal(idx.cpu().numpy().view(np.uint64), want)
-    x = workloads.uniform_u64(n, seed)
-    y = bs.permute(to_device(x), seed)
-    assert_no_device_error()
-    rng = np.random.default_rng(2)
-    js = np.concatenate([np.arange(2048), rng.integers(0, n, 300_000), np.arange(n - 2048, n)])
-    got = y[torch.from_numpy(js).cuda()].cpu().numpy().view(np.uint64)
-    assert np.array_equal(got, x[want[js].astype(np.int64)])
-
-
-@pytest.mark.parametrize("width", [4, 16])
-def test_full_size_other_widths_sampled(width, worst_case_indices):
-    # the sweep's largest sizes for 4- and 16-byte elements through the
-    # default strategy (staged at 2^28, a single pass at 2^28 + 12345)
-    rng = np.random.default_rng(width)
-    for n in (2**28, 2**28 + 12345):
-        x = workloads.sweep_payload(n, width, 0)
-        y = bs.permute(to_device(x), 0)
-        assert_no_device_error()
-        js = np.concatenate([np.arange(2048), rng.integers(0, n, 200_000), np.arange(n - 2048, n)])
-        if n == 2**28:
-            src = oracle.varphilox(js.astype(np.uint64), 28, oracle.round_keys(0, 24)).astype(np.int64)
-        else:
-            src = worst_case_indices[js].astype(np.int64)
-        got = y[torch.from_numpy(js).cuda()].cpu().numpy()
-        want = x[src]
-        assert np.array_equal(got.view(np.uint8).reshape(len(js), -1), want.view(np.uint8).reshape(len(js), -1)), n
-        del y
-
-
-def test_full_size_other_seeds_properties():
-    n = 2**28 + 12345
-    for seed in (1, 4):
-        idx = bs.indices(n, seed, dtype=torch.int64)
-        assert_no_device_error()
-        counts = torch.bincount(idx, minlength=n)
-        assert int(counts.max()) == 1 and int(counts.min()) == 1
-        h = idx.cpu().numpy()
-        _window_check(h, n, seed, [0, 1 << 20, 1 << 27, n - 256])
 
 
 def test_repeated_calls_reuse_workspace():
