@@ -258,9 +258,24 @@ int bshuffle_invert_rows(const uint32_t *idx, uint32_t n, uint64_t rows, uint32_
  * recorded by calls on that stream since the last bshuffle_get_error:
  * BSHUFFLE_OK, BSHUFFLE_ERR_LOOKBACK_TIMEOUT or BSHUFFLE_ERR_DEVICE_BOUNDS (or
  * BSHUFFLE_ERR_CUDA if synchronising failed).  A stream without a workspace
- * has no recorded errors.
+ * has no recorded errors.  It also returns and clears an error that
+ * bshuffle_permute_static recorded on the current device (that entry point
+ * keeps one error word per device): pass the stream of the static call, so
+ * that the call has finished when the word is read.  When both hold an
+ * error, the stream workspace's is returned and both are cleared.
  */
 int bshuffle_get_error(void *stream);
+
+/*
+ * The cudaError_t value (as int) of the CUDA runtime call behind the latest
+ * BSHUFFLE_ERR_CUDA that a bshuffle function returned on the calling thread
+ * (0 if none has), e.g. cudaErrorMemoryAllocation (2) when a workspace could
+ * not be allocated or cudaErrorNoDevice (100) without a GPU.  It stays set
+ * until the next BSHUFFLE_ERR_CUDA on the thread.  bshuffle_cuda_error_name
+ * gives the runtime's name for such a value; never NULL.
+ */
+int bshuffle_last_cuda_error(void);
+const char *bshuffle_cuda_error_name(int error);
 
 /* Static English text for a return code; never NULL. */
 const char *bshuffle_error_string(int code);
@@ -392,9 +407,10 @@ int bshuffle_debug_skip_publish(int64_t tile);
  *              streams at once) race and corrupt each other's output:
  *              serialise them.
  *   Errors.    Argument errors as for bshuffle_permute.  A device-side
- *              look-back timeout is recorded in the array's own error word
- *              and is not reported by bshuffle_get_error (which reads the
- *              per-stream workspaces only).
+ *              error (a look-back wait that ran out of time, an out-of-range
+ *              slot) is recorded in the array's own error word, which
+ *              bshuffle_get_error(stream) syncs, returns and clears for the
+ *              current device.  The word keeps the first error until then.
  */
 int bshuffle_permute_static(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
                             uint32_t rounds, void *stream);

@@ -42,6 +42,8 @@ SIGNATURES = {
     "bshuffle_inverse": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
     "bshuffle_batched": (_int, [_p, _u32, _u32, _u32, _p]),
     "bshuffle_get_error": (_int, [_p]),
+    "bshuffle_last_cuda_error": (_int, []),
+    "bshuffle_cuda_error_name": (_str, [_int]),
     "bshuffle_error_string": (_str, [_int]),
     "bshuffle_domain_bits": (_int, [_u64, ctypes.POINTER(_u32)]),
     "bshuffle_round_keys": (_int, [_u64, _u32, _p]),
@@ -78,7 +80,11 @@ class BShuffleError(RuntimeError):
 
     def __init__(self, code: int, where: str = ""):
         self.code = code
+        self.cuda_error = 0
         msg = error_string(code) if _lib is not None else f"error {code}"
+        if code == BSHUFFLE_ERR_CUDA and _lib is not None:
+            self.cuda_error = _lib.bshuffle_last_cuda_error()
+            msg += f" [{_lib.bshuffle_cuda_error_name(self.cuda_error).decode()}]"
         super().__init__(f"{where}: {msg} (code {code})" if where else f"{msg} (code {code})")
 
 
@@ -158,6 +164,15 @@ def bshuffle_random_gather(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, s
 def bshuffle_get_error(stream: int = 0) -> int:
     """Device-side error recorded on the stream since the last call (0 = none)."""
     return load().bshuffle_get_error(stream)
+
+
+def bshuffle_last_cuda_error() -> int:
+    """cudaError_t behind the latest BSHUFFLE_ERR_CUDA on this thread (0 = none)."""
+    return load().bshuffle_last_cuda_error()
+
+
+def bshuffle_cuda_error_name(error: int) -> str:
+    return load().bshuffle_cuda_error_name(error).decode()
 
 
 def bshuffle_domain_bits(n: int) -> int:

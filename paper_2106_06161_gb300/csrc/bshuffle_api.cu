@@ -102,12 +102,20 @@ struct Workspace {
 std::mutex g_mutex;
 std::map<std::pair<int, uintptr_t>, Workspace> g_workspaces;
 
+// The CUDA error behind the latest BSHUFFLE_ERR_CUDA returned on this thread
+// (bshuffle_last_cuda_error).
+thread_local int g_last_cuda_error = 0;
+
 int cuda_fail(cudaError_t e)
 {
-    (void)e;
-    cudaGetLastError();  // clear the sticky launch error of this thread
+    const cudaError_t pending = cudaGetLastError();  // clears the sticky launch error of this thread
+    g_last_cuda_error = static_cast<int>(e != cudaSuccess ? e : (pending != cudaSuccess ? pending : cudaErrorUnknown));
     return BSHUFFLE_ERR_CUDA;
 }
+
+// Reads and clears the error word of the allocation-free entry point's
+// scratch on `device`, if that scratch has been set up (defined with it below).
+int static_take_error(int device, cudaStream_t stream, int *code);
 
 uint64_t round_up_pow2(uint64_t v)
 {
@@ -706,20 +714,36 @@ int bshuffle_get_error(void *stream_ptr)
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    std::lock_guard<std::mutex> lock(g_mutex);
-    auto it = g_workspaces.find({device, reinterpret_cast<uintptr_t>(stream)});
-    if (it == g_workspaces.end() || it->second.base == nullptr) return BSHUFFLE_OK;
-    WsHeader h{};
-    e = cudaMemcpy(&h, it->second.base, sizeof(h), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (h.error != 0) {
-        const size_t off = offsetof(WsHeader, error);
-        const size_t len = offsetof(WsHeader, error_info) + sizeof(h.error_info) - off;
-        e = cudaMemsetAsync(static_cast<char *>(it->second.base) + off, 0, len, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) return cuda_fail(e);
+    int code = BSHUFFLE_OK;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        auto it = g_workspaces.find({device, reinterpret_cast<uintptr_t>(stream)});
+        if (it != g_workspaces.end() && it->second.base != nullptr) {
+            WsHeader h{};
+            e = cudaMemcpy(&h, it->second.base, sizeof(h), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (h.error != 0) {
+                const size_t off = offsetof(WsHeader, error);
+                const size_t len = offsetof(WsHeader, error_info) + sizeof(h.error_info) - off;
+                e = cudaMemsetAsync(static_cast<char *>(it->second.base) + off, 0, len, stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+                if (e != cudaSuccess) return cuda_fail(e);
+                code = h.error;
+            }
+        }
     }
-    return h.error;
+    // errors of bshuffle_permute_static on this device (its scratch is per device)
+    int static_code = BSHUFFLE_OK;
+    const int rc = static_take_error(device, stream, &static_code);
+    if (rc != BSHUFFLE_OK) return rc;
+    return code != BSHUFFLE_OK ? code : static_code;
+}
+
+int bshuffle_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char *bshuffle_cuda_error_name(int error)
+{
+    return cudaGetErrorName(static_cast<cudaError_t>(error));
 }
 
 const char *bshuffle_error_string(int code)
@@ -876,6 +900,30 @@ int static_scratch(void **out)
         g_static_addr[device] = p;
     }
     *out = g_static_addr[device];
+    return BSHUFFLE_OK;
+}
+
+int static_take_error(int device, cudaStream_t stream, int *code)
+{
+    *code = BSHUFFLE_OK;
+    if (device < 0 || device >= kMaxDevices) return BSHUFFLE_OK;
+    void *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        p = g_static_addr[device];
+    }
+    if (p == nullptr) return BSHUFFLE_OK;  // never used on this device
+    WsHeader h{};
+    cudaError_t e = cudaMemcpy(&h, p, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (h.error != 0) {
+        const size_t off = offsetof(WsHeader, error);
+        const size_t len = offsetof(WsHeader, error_info) + sizeof(h.error_info) - off;
+        e = cudaMemsetAsync(static_cast<char *>(p) + off, 0, len, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+        *code = h.error;
+    }
     return BSHUFFLE_OK;
 }
 

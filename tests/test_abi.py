@@ -103,6 +103,14 @@ def test_no_device_means_cuda_error(lib):
     buf = (ctypes.c_uint64 * 64)()
     a = ctypes.addressof(buf)
     assert lib.bshuffle_permute(a, a + 256, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_CUDA
+    # the cause is kept: the CUDA runtime's error of the failed call
+    cause = lib.bshuffle_last_cuda_error()
+    assert cause != 0
+    name = lib.bshuffle_cuda_error_name(cause).decode()
+    assert name.startswith("cuda") and name != "cudaSuccess"
+    with pytest.raises(L.BShuffleError) as err:
+        L.bshuffle_permute(a, a + 256, 4, 8, 0)
+    assert err.value.cuda_error == cause and name in str(err.value)
 
 
 def test_binding_has_no_cpu_fallback():
