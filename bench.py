@@ -194,22 +194,31 @@ def cpu_oracle_sample(slots: int, trials: int):
 
 
 def run_reference(args):
-    rank, world, _ = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
+    """The CPU oracle, as it stands, on this workload: every step is the whole
+    n = 2^28 uint64 shuffle by the threaded oracle on all host cores (count
+    per domain range, exclusive scan, gather)."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    slots = 2**20
-    times = cpu_oracle_sample(slots, args.warmup + args.steps)[args.warmup:]
+    import oracle
+    cores = oracle.default_threads()
+    host = workloads.uniform_u64(N_MAIN, SEED)
+    times = []
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.permute_mt(host, SEED, ROUNDS, threads=cores)
+        times.append(time.perf_counter() - t0)
+    times = times[args.warmup:]
     total = sum(times)
-    value = slots * len(times) / total
+    value = N_MAIN * len(times) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "elements/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "bijective shuffle of n=2^28 uniform uint64 keys, seed 0, 24 rounds",
-                   "n": N_MAIN, "elem_bytes": ELEM},
-        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {slots} output slots of the n=2^28 uint64 shuffle per step"},
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": workload_config(args.gpus),
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle",
+                         "sample": "the whole n=2^28 uint64 shuffle per step, threaded oracle on "
+                                   f"{cores} host threads"},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -247,47 +256,59 @@ def traffic_for(kernel: str, fingerprint: str):
     return rec.get("dram_bytes_per_launch")
 
 
-# Integer issue peak of the cipher on GB300: 152 SMs x 4 schedulers x 32
-# lanes at the 2070 MHz maximum clock, over the operations one evaluation
-# needs as written (24 rounds; per even-k round the forward cipher takes two
-# product words, two XORs and one AND = 5, the inverse one more product word
-# and one more AND = 7).
-SMS, LANES_PER_SM, SM_HZ = 152, 128, 2.07e9
-FORWARD_OPS_PER_EVAL = 24 * 5
-INVERSE_OPS_PER_EVAL = 24 * 7
+# Pass 1 of the staged path is bound by integer issue: 2^28 inverse cipher
+# evaluations per launch.  ncu on that kernel (n = 2^26 uint64, even k) puts
+# the FMA-heavy pipe, which issues the integer multiplies, at the top of the
+# pipes (sm__pipe_fmaheavy_cycles_active); its peak rate is one warp
+# instruction every two cycles per SM sub-partition (16 lanes).  The derived
+# peak is the evaluation rate at which that pipe is busy every cycle:
+#   152 SMs x 4 sub-partitions x 16 lanes x 2.07 GHz
+#   / (FMA-heavy thread instructions per evaluation, counted by ncu as
+#      smsp__inst_executed_pipe_fmaheavy.sum x 32 / evaluations).
+SMS, SMSP_PER_SM, FMAHEAVY_LANES, SM_HZ = 152, 4, 16, 2.07e9
+FMAHEAVY_INST_PER_INVERSE_EVAL = 72.0
 
 
-def roofline_for(passes, bsbuild, strategy, window_scatter_ms=None):
+def alu_peak_evals_per_s() -> float:
+    return SMS * SMSP_PER_SM * FMAHEAVY_LANES * SM_HZ / FMAHEAVY_INST_PER_INVERSE_EVAL
+
+
+def roofline_for(passes, bsbuild, strategy, window_scatter_ms=None, step_ms=None):
     """Roofline of the dominant kernel of one step, plus every pass's line.
 
-    The staged scatter pass also gets its fraction of the window-scatter
-    kernel (the same sequential reads and random writes into 8 MiB windows
-    with nothing else), the L2 random-write ceiling it runs into."""
+    Algorithmic bytes are the metric's: 2 n elem_bytes per shuffle (one read
+    and one write of every element), whichever kernels move them.  The staged
+    path's own intermediate traffic (value and slot written by pass 1 and
+    read by pass 2: 20 B per uint64 element and pass) is reported beside it,
+    not as algorithmic.  The staged scatter pass also gets its fraction of
+    the window-scatter kernel (the same sequential reads and random writes
+    into 8 MiB windows with nothing else), the L2 random-write ceiling it
+    runs into."""
     peak, peak_kind = measured_peaks()
-    n, k = N_MAIN, 28
+    n = N_MAIN
+    algo = 2 * n * ELEM
     if len(passes) == 1 and strategy == STRATEGIES["single_pass"]:
-        names = [("elem_tile_kernel<uint64, Gather, even k>", "kernels_elem.cu", "hbm", 2 * n * ELEM, None)]
+        names = [("elem_tile_kernel<uint64, Gather, even k>", "kernels_elem.cu", "hbm", None)]
     elif len(passes) == 1:
-        names = [("pipe_tile_kernel<uint64, even k>", "kernels_pipe.cu", "hbm", 2 * n * ELEM, None)]
+        names = [("pipe_tile_kernel<uint64, even k>", "kernels_pipe.cu", "hbm", None)]
     else:
-        names = [("staged_bucket_kernel<uint64, even k>", "kernels_staged.cu", "alu", 2**k, n * (ELEM + ELEM + 4)),
-                 ("staged_scatter_kernel<uint64>", "kernels_staged.cu", "hbm", n * (ELEM + 4 + ELEM), None)]
+        names = [("staged_bucket_kernel<uint64, even k>", "kernels_staged.cu", "alu", n * (ELEM + ELEM + 4)),
+                 ("staged_scatter_kernel<uint64>", "kernels_staged.cu", "hbm", n * (ELEM + 4 + ELEM))]
     lines = []
-    for ms, (name, src, bound, work, bytes_) in zip(passes, names):
+    for ms, (name, src, bound, staged_bytes) in zip(passes, names):
+        gbps = algo / (ms * 1e-3) / 1e9
+        line = {"kernel": name, "bound": bound, "ms": ms, "algorithmic_bytes_per_launch": algo,
+                "achieved_gbps": gbps, "frac": gbps / peak}
+        if staged_bytes is not None:
+            sg = staged_bytes / (ms * 1e-3) / 1e9
+            line.update(staged_bytes_per_launch=staged_bytes, staged_gbps=sg, staged_frac=sg / peak)
         if bound == "alu":
-            achieved = work / (ms * 1e-3)
-            pk = SMS * LANES_PER_SM * SM_HZ / INVERSE_OPS_PER_EVAL
-            line = {"kernel": name, "bound": "alu", "ms": ms, "achieved": achieved, "peak": pk,
-                    "unit": "inverse cipher evaluations/s", "frac": achieved / pk,
-                    "algorithmic_evals_per_launch": work,
-                    "peak_kind": "derived: 152 SMs x 128 lanes x 2.07 GHz / 168 ops per inverse evaluation",
-                    "hbm_gbs": bytes_ / (ms * 1e-3) / 1e9, "hbm_frac": bytes_ / (ms * 1e-3) / 1e9 / peak,
-                    "algorithmic_bytes_per_launch": bytes_}
-        else:
-            achieved = work / (ms * 1e-3) / 1e9
-            line = {"kernel": name, "bound": "hbm", "ms": ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "algorithmic_bytes_per_launch": work,
-                    "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+            evals = float(2**28)
+            pk = alu_peak_evals_per_s()
+            line["alu"] = {"evaluations_per_launch": evals, "achieved": evals / (ms * 1e-3), "peak": pk,
+                           "unit": "inverse cipher evaluations/s", "frac": evals / (ms * 1e-3) / pk,
+                           "peak_kind": "derived: 152 SMs x 4 x 16 FMA-heavy lanes x 2.07 GHz / "
+                                        f"{FMAHEAVY_INST_PER_INVERSE_EVAL:g} FMA-heavy instructions per evaluation"}
         line["traffic"] = traffic_for(name, bsbuild.kernel_fingerprint(src))
         if name.startswith("staged_scatter") and window_scatter_ms:
             line["window_scatter_ms"] = window_scatter_ms
@@ -295,10 +316,20 @@ def roofline_for(passes, bsbuild, strategy, window_scatter_ms=None):
             line["frac_of_window_scatter"] = window_scatter_ms / ms
         lines.append(line)
     dom = max(lines, key=lambda d: d["ms"])
-    roof = {key: dom[key] for key in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
-    roof["kernel"] = dom["kernel"]
-    roof["launch_ms"] = dom["ms"]
-    roof["peak_kind"] = dom["peak_kind"]
+    roof = {"bound": "hbm", "achieved": dom["achieved_gbps"], "peak": peak, "unit": "GB/s",
+            "frac": dom["frac"], "traffic": dom["traffic"], "kernel": dom["kernel"], "launch_ms": dom["ms"],
+            "algorithmic_bytes_per_launch": algo,
+            "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "kernel_binding_unit": dom["bound"]}
+    if dom["traffic"]:
+        roof["traffic_over_algorithmic"] = dom["traffic"] / algo
+    if step_ms:
+        roof["step_ms"] = step_ms
+        roof["step_frac"] = algo / (step_ms * 1e-3) / 1e9 / peak
+    traffic = [ln["traffic"] for ln in lines]
+    if all(traffic):
+        roof["step_traffic"] = sum(traffic)
+        roof["step_traffic_over_algorithmic"] = sum(traffic) / algo
     return roof, lines
 
 
@@ -368,56 +399,149 @@ def run_ours(args):
     for _ in range(3):
         ws()
     _, ws_region = timed_launches(ws, 10, stream, torch)
-    roofline, pass_lines = roofline_for(passes, bsbuild, bs.bshuffle_get_strategy(), ws_region / 10)
+    roofline, pass_lines = roofline_for(passes, bsbuild, bs.bshuffle_get_strategy(), ws_region / 10,
+                                        ms_per_step)
 
     e2e = e2e_pipeline(bs, torch, dev, host, seed, args, world)
 
     extra = {}
     if not args.no_extra and rank == 0:
         extra = secondary(bs, torch, dev, stream)
+        extra["sweep"] = sweep(bs, torch, dev, stream)
         bs.bshuffle_set_strategy(STRATEGIES[args.strategy])
 
-    cpu = None
-    if rank == 0 and world == 1:
-        slots = 2**21
-        times = cpu_oracle_sample(slots, 8)
-        cores = 1
-        cpu = {"value": slots * len(times) / sum(times), "unit": "elements/s", "cores": cores,
-               "kind": "oracle",
-               "sample": f"first {slots} output slots of the same n=2^28 uint64 shuffle, 8 trials, "
-                         f"single-threaded C oracle"}
-        # context: a sequential Fisher-Yates shuffle (the classical method of
-        # Sec. 1) of 2^22 uint64 keys, single thread
-        import oracle
-        fy = workloads.uniform_u64(2**22, 5)
-        fy_t = []
-        for t in range(3):
-            t0 = time.perf_counter()
-            oracle.fisher_yates(fy, t)
-            fy_t.append(time.perf_counter() - t0)
-        cpu["fisher_yates_2p22_u64_elements_per_s"] = 2**22 / min(fy_t)
+    cpu = cpu_baseline(host) if rank == 0 and world == 1 else None
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic",
-            "config": {"workload": "bijective shuffle of n=2^28 uniform uint64 keys per GPU, seed 0, 24 rounds",
-                       "n": N_MAIN, "elem_bytes": ELEM, "rounds": ROUNDS,
-                       "l2": "inputs (2 GiB) larger than L2, no flush",
-                       "parallelism": f"independent shuffles, {world} GPU(s)"},
+            "data": "synthetic", "config": workload_config(world),
             "logical_gbps": 2 * N_MAIN * ELEM / (ms_per_step * 1e-3) / 1e9,
             "strategy": {0: "auto", 1: "single_pass", 2: "staged", 3: "pipelined"}[bs.bshuffle_get_strategy()],
-            "kernels_per_step": len(passes), "roofline": roofline, "passes": pass_lines,
-            "single_pass_tuning": tuning,
+            "kernels_per_step": len(passes), "passes": pass_lines,
+            "single_pass_tuning": tuning, "extra": extra,
             "e2e": e2e, "gpu_launches": args.steps * len(passes), "clocks": clk,
-            "cpu_baseline": cpu, "extra": extra,
+            "cpu_baseline": cpu, "roofline": roofline,
         }
+        # the last key holds the figures a reader of the line's tail needs
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def workload_config(world: int) -> dict:
+    """The bench line's config, the same for the GPU arm and the reference arm."""
+    return {"workload": "bijective shuffle of n=2^28 uniform uint64 keys per GPU, seed 0, 24 rounds",
+            "n": N_MAIN, "elem_bytes": ELEM, "rounds": ROUNDS,
+            "l2": "inputs (2 GiB) larger than L2, no flush",
+            "parallelism": f"independent shuffles, {world} GPU(s)"}
+
+
+def cpu_baseline(host):
+    """The oracle on the host cores: Algorithm 1 on every core over the whole
+    workload (count per domain range, exclusive scan, gather: the multi-core
+    form of the method), the sequential oracle on the first slots, and a
+    sequential Fisher-Yates shuffle (the classical method of Sec. 1) of the
+    same n = 2^28 uint64 keys."""
+    import oracle
+    cores = oracle.default_threads()
+    t0 = time.perf_counter()
+    out = oracle.permute_mt(host, SEED, ROUNDS, threads=cores)
+    mt_s = time.perf_counter() - t0
+    del out
+    slots = 2**21
+    st = cpu_oracle_sample(slots, 4)
+    fy = []
+    for t in range(2):
+        t0 = time.perf_counter()
+        oracle.fisher_yates(host, t)
+        fy.append(time.perf_counter() - t0)
+    return {"value": N_MAIN / mt_s, "unit": "elements/s", "cores": cores, "kind": "oracle",
+            "sample": f"the whole n=2^28 uint64 shuffle (seed 0) once, threaded oracle on {cores} host threads "
+                      "(count per domain range, exclusive scan, gather)",
+            "seconds": mt_s,
+            "single_thread": {"value": slots * len(st) / sum(st), "unit": "elements/s", "cores": 1,
+                              "sample": f"first {slots} output slots of the same shuffle, {len(st)} trials"},
+            "fisher_yates": {"value": N_MAIN / min(fy), "unit": "elements/s", "cores": 1,
+                             "sample": "sequential Fisher-Yates (mt19937_64) of the same 2^28 uint64 keys, "
+                                       f"best of {len(fy)}"}}
+
+
+def summary(line: dict) -> dict:
+    """Compact figures, printed last so that the tail of the line shows them."""
+    ex = line.get("extra") or {}
+    roof = line["roofline"]
+    out = {"elements_per_s": line["value"], "ms_per_step": line["ms_per_step"],
+           "hbm_frac_step": roof.get("step_frac"), "hbm_frac_dominant_kernel": roof["frac"],
+           "dominant_kernel": roof["kernel"]}
+    for key in ("2p28_u64", "worst_case_2p28_plus_12345_u64"):
+        row = {name: round(ex[f"{key}_{name}"]["ms"], 3) for name in ("single_pass", "pipelined", "staged")
+               if f"{key}_{name}" in ex}
+        if row:
+            out[f"{key}_ms"] = row
+    sw = ex.get("sweep")
+    if sw:
+        out["sweep_gelem_per_s"] = {w: {n: round(r["elements_per_s_mean"] / 1e9, 2) for n, r in rows.items()}
+                                    for w, rows in sw["rows"].items()}
+    b = ex.get("batched_4096_uneven_int32")
+    if b:
+        out["batched_speedup"] = round(b["speedup"], 2)
+    cpu = line.get("cpu_baseline")
+    if cpu:
+        out["cpu_elements_per_s"] = {"oracle_threads": cpu["value"], "cores": cpu["cores"],
+                                     "oracle_1_thread": cpu["single_thread"]["value"],
+                                     "fisher_yates": cpu["fisher_yates"]["value"]}
+    out["e2e_elements_per_s"] = line["e2e"]["value"]
+    return out
+
+
+SWEEP_LABELS = {2**10: "2^10", 2**16: "2^16", 2**20: "2^20", 2**24: "2^24", 2**28: "2^28",
+                2**28 + 12345: "2^28+12345"}
+
+
+def sweep(bs, torch, dev, stream, trials=5):
+    """Config 2's sweep through the default strategy: 4, 8 and 16-byte
+    elements at n in {2^10, 2^16, 2^20, 2^24, 2^28, 2^28 + 12345}.  A trial
+    times a run of back-to-back launches (at least about 2 ms of work, so
+    that small lengths measure throughput, not one launch); the line gives
+    the mean and median of 5 trials (Sec. 6 reports means of 5 trials).
+    Inputs below the 129 MB L2 stay resident between launches, as in any
+    repeated-launch measurement; payload values do not affect the timing."""
+    peak, _ = measured_peaks()
+    sptr = stream.cuda_stream
+    rows = {}
+    for width in (4, 8, 16):
+        wrow = {}
+        for n in workloads.SWEEP_SIZES:
+            cols = width // 8 if width == 16 else 1
+            dt = torch.int32 if width == 4 else torch.int64
+            shape = (n, cols) if width == 16 else (n,)
+            x = torch.randint(-2**31, 2**31 - 1, shape, dtype=dt, device=dev)
+            y = torch.empty_like(x)
+            xp, yp = x.data_ptr(), y.data_ptr()
+            f = lambda: bs.bshuffle_permute(xp, yp, n, width, 0, ROUNDS, sptr)  # noqa: E731
+            reps = max(3, min(2000, (2**22 * 16) // (n * width) + 1))
+            for _ in range(3):
+                f()
+            per_elem = []
+            for _ in range(trials):
+                _, region = timed_launches(f, reps, stream, torch)
+                per_elem.append(n * reps / (region * 1e-3))
+            mean = statistics.mean(per_elem)
+            med = statistics.median(per_elem)
+            wrow[SWEEP_LABELS[n]] = {
+                "elements_per_s_mean": mean, "elements_per_s_median": med, "launches_per_trial": reps,
+                "logical_gbps_mean": mean * 2 * width / 1e9, "hbm_frac_mean": mean * 2 * width / 1e9 / peak}
+            del x, y
+        rows[f"{width}B"] = wrow
+    if bs.get_error() != 0:
+        raise SystemExit("device error during the sweep")
+    return {"strategy": "auto", "trials": trials, "rows": rows,
+            "note": "elements/s = n x launches / region time; logical bytes 2 n elem_bytes per launch"}
 
 
 def e2e_pipeline(bs, torch, dev, host, seed, args, world):
