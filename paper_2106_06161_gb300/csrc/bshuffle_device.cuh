@@ -115,16 +115,20 @@ static_assert(static_cast<uint32_t>(kM0) * kM0InvLo == 1u, "M0 inverse");
 // word.  The left half must be exact; the right half may carry don't-care
 // bits above its width (only its low L + 1 bits are read, and the product
 // with M0^-1 is masked to L bits), so it is masked once after the last round.
+// For odd k the round moves b to bit L with a multiply by lift_mul = 2^L, a
+// run-time value, so that it runs on the FMA pipe: with a shift, the ALU pipe
+// bound odd-k inverse rounds (measured on GB300: 2.22 -> 1.87 ms per 2^28
+// evaluations at k = 29).
 template <bool ODD>
 __device__ __forceinline__ void cipher_inverse_round(uint32_t &left, uint32_t &right, uint32_t key,
-                                                     uint32_t L, uint32_t lmask)
+                                                     uint32_t lift_mul, uint32_t lmask)
 {
     const uint32_t bl = ODD ? (right >> 1) : right;
     const uint32_t old_left = (bl * kM0InvLo) & lmask;
     const uint32_t hi = __umulhi(static_cast<uint32_t>(kM0), old_left) + static_cast<uint32_t>(kM0 >> 32) * old_left;
     const uint32_t x = left ^ hi ^ key;
     // odd k: R in the low L bits and b (bit 0 of the old right half) at bit L
-    right = ODD ? ((x & lmask) | ((right << L) & ~lmask)) : x;
+    right = ODD ? ((x & lmask) | ((right * lift_mul) & ~lmask)) : x;
     left = old_left;
 }
 
@@ -133,11 +137,11 @@ template <bool ODD, int ITEMS>
 __device__ __forceinline__ void cipher_inverse_items_loop(uint32_t (&left)[ITEMS], uint32_t (&right)[ITEMS],
                                                           const uint32_t *keys, uint32_t rounds, const Geometry &g)
 {
-    const uint32_t L = g.L, lmask = g.lmask;
+    const uint32_t lift_mul = g.lift_mul, lmask = g.lmask;
     for (uint32_t r = rounds; r-- > 0;) {
         const uint32_t key = keys[r];
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) cipher_inverse_round<ODD>(left[j], right[j], key, L, lmask);
+        for (int j = 0; j < ITEMS; ++j) cipher_inverse_round<ODD>(left[j], right[j], key, lift_mul, lmask);
     }
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) right[j] &= g.rmask;
@@ -150,7 +154,7 @@ __device__ __forceinline__ void cipher_inverse_items_fixed(uint32_t (&left)[ITEM
 #pragma unroll
     for (int r = ROUNDS - 1; r >= 0; --r) {
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) cipher_inverse_round<ODD>(left[j], right[j], keys[r], g.L, g.lmask);
+        for (int j = 0; j < ITEMS; ++j) cipher_inverse_round<ODD>(left[j], right[j], keys[r], g.lift_mul, g.lmask);
     }
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) right[j] &= g.rmask;

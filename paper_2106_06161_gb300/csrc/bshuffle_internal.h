@@ -34,7 +34,7 @@ struct Geometry {
     uint32_t rmask;    // 2^R - 1
     uint64_t domain;   // 2^k
     uint32_t odd_mul;  // 2^(31 - L): multiplying by it moves bit L to bit 31
-    uint32_t pad0;
+    uint32_t lift_mul; // 2^L: multiplying by it moves bit 0 to bit L
 };
 
 // Everything one fused tile launch needs, passed by value (param space).
@@ -135,19 +135,22 @@ cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream);
 
 // ------------------------------------------------------------------ staged path
 
-// The staged shuffle of power-of-two lengths (n == 2^k): same output as the
-// fused single pass, two streaming passes (see kernels_staged.cu).
+// The staged shuffle: same output as the fused single pass, two streaming
+// passes (see kernels_staged.cu).  For n == 2^k a bucket is a window of
+// output slots; for other n (the ranked form) a bucket is a window of domain
+// indices, and the second pass ranks its kept indices with a bitmap.
 struct StagedArgs {
     const void *in;
     void *out;
-    Geometry g;             // g.n == g.domain
+    Geometry g;             // g.n <= g.domain
     uint32_t rounds;
-    uint32_t dst_shift;     // log2 of a destination bucket (output window) in elements
-    uint32_t num_dst;       // destination buckets, <= 4096
-    uint32_t pad0;
-    void *dval;             // n values, destination-bucket major
-    uint32_t *dpos;         // n slot offsets within their destination bucket
+    uint32_t dst_shift;     // log2 of a bucket's span (output slots, or domain indices when ranked)
+    uint32_t num_dst;       // buckets, <= 4096
+    uint32_t sub_shift;     // ranked: log2 of the domain indices one pass-2 CTA ranks (<= dst_shift)
+    void *dval;             // values, bucket-major, 2^dst_shift entries reserved per bucket
+    uint32_t *dpos;         // offsets within the bucket's span
     uint32_t *dst_cursor;   // num_dst, zero at launch
+    uint32_t *bucket_base;  // ranked: num_dst first slots, written by pass 2a
     WsHeader *ws;           // error word
     uint32_t keys[kMaxRounds];
 };
@@ -156,6 +159,9 @@ uint32_t staged_tile_size();
 // log2 of the destination bucket (output window) in elements for a staged
 // shuffle of n = 2^k elements of elem_bytes.
 uint32_t staged_window_shift(uint64_t n, uint32_t elem_bytes);
+// The ranked form (n < 2^k): log2 of a bucket's span of domain indices and of
+// the span one pass-2 CTA ranks, for n elements of elem_bytes on a 2^k domain.
+void staged_rank_shifts(uint64_t n, uint32_t k, uint32_t elem_bytes, uint32_t *bucket_shift, uint32_t *sub_shift);
 // Enqueue the two passes (elem_bytes 4, 8 or 16) of the shuffle, or of the
 // inverse shuffle when `inverse`; the caller zeroes the cursors first.
 // marks, when not null, are 3 events recorded before P1, between the passes

@@ -212,6 +212,7 @@ __device__ __forceinline__ void resolve_job(const BatchArgs &a, uint32_t ticket,
             job.g.rmask = (k - k / 2) >= 32 ? 0xffffffffu : ((1u << (k - k / 2)) - 1u);
             job.g.domain = uint64_t{1} << k;
             job.g.odd_mul = 1u << (31u - k / 2);
+            job.g.lift_mul = 1u << (k / 2);
             job.seed = d.seed;
             job.instance = t;
             job.ticket = ticket;
