@@ -17,11 +17,11 @@
  * the "Bijective2" variant of Sec. 6), the gather of each kept element once,
  * and a coalesced store into its compacted slot.  By default the library
  * picks among variants with the same output (see bshuffle_set_strategy):
- * inputs much larger than L2 of power-of-two length run a staged two-pass
- * variant; other power-of-two lengths run one launch without the scan (with
- * nothing dropped, slot j holds X[f(j)]); other lengths run the single pass,
- * pipelined on large domains (a dedicated warp per CTA does the look-back
- * while the other warps evaluate the next tile).
+ * inputs much larger than L2 run a staged variant whose HBM accesses are all
+ * sequential; other power-of-two lengths run one launch without the scan
+ * (with nothing dropped, slot j holds X[f(j)]); other lengths run the single
+ * pass, pipelined on large domains (a dedicated warp per CTA does the
+ * look-back while the other warps evaluate the next tile).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -301,15 +301,21 @@ int bshuffle_release_workspaces(void);
  *       decoupled look-back, one random read and one coalesced write per
  *       element (the paper's "Bijective2", Sec. 6).  No extra memory beyond
  *       the small workspace.
- *   BSHUFFLE_STRATEGY_STAGED  for n = 2^k >= 4096 and 4, 8 or 16-byte
- *       elements (other calls run the single pass): nothing is dropped, so
- *       element b belongs in slot f^-1(b) (the inverse cipher of Sec. 3.2;
+ *   BSHUFFLE_STRATEGY_STAGED  for n >= 4096 and 4, 8 or 16-byte elements
+ *       (other calls run the single pass).  For n = 2^k nothing is dropped,
+ *       so element b belongs in slot f^-1(b) (the inverse cipher of Sec. 3.2;
  *       bshuffle_inverse uses the same passes with slot f(b)).
  *       Pass 1 reads the input sequentially, inverts the cipher and buckets
  *       (value, slot) by 8 MiB output window; pass 2 scatters each window
  *       while it is resident in L2.  Random HBM accesses are rate-limited on
  *       GB300, streaming ones are not.  Workspace n * (4 + elem_bytes) bytes
- *       plus a little, allocated on first use per stream.
+ *       plus a little, allocated on first use per stream.  Other n (the
+ *       ranked form, bshuffle_permute only): element b's slot is the rank of
+ *       its domain index i = f^-1(b) among the kept indices (Algorithm 1's
+ *       exclusive scan); pass 1 buckets (value, i) by span of domain
+ *       indices, a second kernel ranks each span's kept indices with a
+ *       bitmap in shared memory, and the window scatter places the values.
+ *       Workspace 2^k * (4 + elem_bytes) bytes plus a little.
  *   BSHUFFLE_STRATEGY_PIPELINED  the single pass with its look-back taken
  *       off the compute warps, for gathers and scatters of 4, 8 and 16-byte
  *       elements and for indices (other calls run the plain single pass):
@@ -319,7 +325,9 @@ int bshuffle_release_workspaces(void);
  *       with the look-back.  Same memory traffic and workspace as the single
  *       pass.
  *   BSHUFFLE_STRATEGY_AUTO (default)  staged when it applies and
- *       n * elem_bytes >= 256 MiB; otherwise, for n = 2^k >= 16, one launch
+ *       n * elem_bytes >= 256 MiB (for n other than 2^k: with 4- or 8-byte
+ *       elements only; 16-byte elements run faster on the pipelined single
+ *       pass there); otherwise, for n = 2^k >= 16, one launch
  *       without the scan (nothing is dropped, so the i-th domain index is
  *       the i-th kept one: out[i] = in[f(i)], out[f(i)] = in[i] or
  *       out[i] = f(i)); otherwise the pipelined single pass where it applies

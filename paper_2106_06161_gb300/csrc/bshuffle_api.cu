@@ -31,6 +31,14 @@ std::atomic<int> g_strategy{BSHUFFLE_STRATEGY_AUTO};
 std::atomic<int> g_pass_timing{0};
 // Auto strategy: the staged path from this many input bytes on.
 constexpr uint64_t kStagedMinBytes = uint64_t{1} << 28;
+// Auto strategy: lengths that are not powers of two take the staged path's
+// ranked form for 4- and 8-byte elements (from the same input size), else the
+// pipelined single pass.  Measured on GB300 against the pipelined single
+// pass: uint64 at 2^25 + 1, 2^26 + 1, 2^27 + 1, 2^28 + 12345: 0.535 / 1.19 /
+// 2.17 / 5.09 ms against 0.583 / 1.35 / 2.79 / 5.86 ms; uint32 at
+// 2^28 + 12345 and 2^29 + 3: 4.70 / 9.18 ms against 5.52 / 11.24 ms.  With
+// 16-byte elements the ranked form lost (7.6 against 6.2 ms at 2^28 + 12345).
+bool ranked_by_default(uint32_t elem_bytes) { return elem_bytes == 4 || elem_bytes == 8; }
 // Auto strategy: the pipelined single pass from these domain exponents on.
 // On smaller domains a launch is all latency, and the plain kernel, without
 // the hand-offs between compute warps and look-back warp, finishes first:
@@ -78,6 +86,7 @@ Geometry geometry_of(uint64_t n)
     g.rmask = g.R >= 32 ? 0xffffffffu : ((1u << g.R) - 1u);
     g.domain = uint64_t{1} << g.k;
     g.odd_mul = 1u << (31u - g.L);
+    g.lift_mul = 1u << g.L;
     return g;
 }
 
@@ -336,18 +345,32 @@ int run_staged(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint6
     a.in = in;
     a.out = out;
     a.g = geometry_of(n);
-    if (a.g.domain != n) return BSHUFFLE_ERR_INVALID;
+    // n < 2^k: the ranked form (gathers only), buckets are spans of domain indices
+    const bool padded = a.g.domain != n;
+    if (padded && inverse) return BSHUFFLE_ERR_INVALID;
     a.rounds = rounds;
     fill_keys(seed, rounds, a.keys);
-    const uint32_t shift = bsh::staged_window_shift(n, elem_bytes);
-    a.dst_shift = shift;
-    a.num_dst = static_cast<uint32_t>((n + (uint64_t{1} << shift) - 1) >> shift);
+    if (padded) {
+        uint32_t shift = 0, sub = 0;
+        bsh::staged_rank_shifts(n, a.g.k, elem_bytes, &shift, &sub);
+        a.dst_shift = shift;
+        a.sub_shift = sub;
+        a.num_dst = static_cast<uint32_t>(a.g.domain >> shift);
+    } else {
+        const uint32_t shift = bsh::staged_window_shift(n, elem_bytes);
+        a.dst_shift = shift;
+        a.sub_shift = shift;
+        a.num_dst = static_cast<uint32_t>((n + (uint64_t{1} << shift) - 1) >> shift);
+    }
 
+    // every bucket reserves its whole span: 2^k entries for the ranked form
+    const uint64_t entries = padded ? a.g.domain : n;
     auto up = [](size_t v) { return (v + 255) & ~static_cast<size_t>(255); };
     const size_t off_dval = 0;
-    const size_t off_dpos = up(off_dval + n * elem_bytes);
-    const size_t off_cursor = up(off_dpos + n * sizeof(uint32_t));
-    const size_t total = up(off_cursor + a.num_dst * sizeof(uint32_t));
+    const size_t off_dpos = up(off_dval + entries * elem_bytes);
+    const size_t off_cursor = up(off_dpos + entries * sizeof(uint32_t));
+    const size_t off_base = up(off_cursor + a.num_dst * sizeof(uint32_t));
+    const size_t total = up(off_base + a.num_dst * sizeof(uint32_t));
 
     Workspace *ws = nullptr;
     int rc = acquire_workspace(stream, kMinStatusWords, &ws);
@@ -358,6 +381,7 @@ int run_staged(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint6
     a.dval = base + off_dval;
     a.dpos = reinterpret_cast<uint32_t *>(base + off_dpos);
     a.dst_cursor = reinterpret_cast<uint32_t *>(base + off_cursor);
+    a.bucket_base = reinterpret_cast<uint32_t *>(base + off_base);
     a.ws = ws->header();
     cudaError_t e = cudaMemsetAsync(a.dst_cursor, 0, a.num_dst * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -374,6 +398,14 @@ bool staged_eligible(uint64_t n, uint32_t elem_bytes)
 {
     return (elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 16) && n >= 2 * bsh::staged_tile_size() &&
            (n & (n - 1)) == 0;
+}
+
+// Its ranked form serves the other lengths of the shuffle (not the inverse):
+// the slot of a kept domain index is its rank among the kept indices.
+bool ranked_eligible(uint64_t n, uint32_t elem_bytes)
+{
+    return (elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 16) && n >= 2 * bsh::staged_tile_size() &&
+           (n & (n - 1)) != 0;
 }
 
 }  // namespace
@@ -410,9 +442,11 @@ int bshuffle_permute(const void *in, void *out, uint64_t n, uint32_t elem_bytes,
     rc = check_buffers(in, out, n, elem_bytes);
     if (rc != BSHUFFLE_OK) return rc;
     const int strategy = g_strategy.load();
-    if (strategy != BSHUFFLE_STRATEGY_SINGLE_PASS && strategy != BSHUFFLE_STRATEGY_PIPELINED &&
-        staged_eligible(n, elem_bytes) &&
-        (strategy == BSHUFFLE_STRATEGY_STAGED || n * elem_bytes >= kStagedMinBytes)) {
+    const bool staged =
+        (strategy == BSHUFFLE_STRATEGY_STAGED && (staged_eligible(n, elem_bytes) || ranked_eligible(n, elem_bytes))) ||
+        (strategy == BSHUFFLE_STRATEGY_AUTO && n * elem_bytes >= kStagedMinBytes &&
+         (staged_eligible(n, elem_bytes) || (ranked_by_default(elem_bytes) && ranked_eligible(n, elem_bytes))));
+    if (staged) {
         rc = run_staged(in, out, n, elem_bytes, seed, rounds, stream);
         if (rc == BSHUFFLE_OK || strategy == BSHUFFLE_STRATEGY_STAGED) return rc;
         // auto: the staged buffers could not be had; the single pass needs none

@@ -6,7 +6,8 @@ them (library default strategy, 24 rounds):
 * n = 2^28: nothing is dropped, so the default runs the staged two-pass path
   for 4-, 8- and 16-byte elements (256 output windows for uint64);
 * n = 2^28 + 12345: domain 2^29 with about half of the images dropped (the
-  paper's worst-case padding), run by the pipelined single pass.
+  paper's worst-case padding), run by the staged path's ranked form for 4-
+  and 8-byte elements and by the pipelined single pass for 16-byte ones.
 
 For every seed 0..4 of the sweep, every one of the n output slots of the
 uint64 shuffle and of the 64-bit index output is compared with one full pass

@@ -1,10 +1,12 @@
-"""The staged strategy of bshuffle_permute (for n = 2^k: the inverse cipher
-turns the gather into a scatter with a sequential source side, then an
-L2-resident window scatter) must produce exactly the single pass's output:
-checked against the oracle across widths and sizes, against the single pass
-and the oracle at larger sizes, and through the automatic choice at full
-size (test_gpu_full_size.py).  Lengths that are not powers of two
-must run the single pass under the staged setting."""
+"""The staged strategy of bshuffle_permute must produce exactly the single
+pass's output.  For n = 2^k the inverse cipher turns the gather into a
+scatter with a sequential source side, then an L2-resident window scatter;
+for other n (the ranked form) pass 1 buckets each element by the span of
+domain indices its preimage falls in, and pass 2 ranks the kept indices of a
+span with a bitmap (spans larger than one CTA's bitmap are split over a
+cluster of CTAs).  Checked against the oracle across widths and sizes,
+against the single pass and the oracle at larger sizes, and through the
+automatic choice at full size (test_gpu_full_size.py)."""
 import numpy as np
 import pytest
 import torch
@@ -45,6 +47,49 @@ def test_staged_matches_oracle(bs, width):
             assert np.array_equal(got, oracle.permute(x, seed)), (n, seed)
 
 
+def _passes(bs, xd, seed, strategy, rounds=24):
+    """Output and the number of passes the call ran (2 for the staged path)."""
+    stream = torch.cuda.current_stream().cuda_stream
+    bs.bshuffle_set_strategy(strategy)
+    bs.bshuffle_set_pass_timing(True)
+    try:
+        y = bs.permute(xd, seed, rounds)
+        passes = len(bs.bshuffle_last_pass_ms(stream))
+        assert_no_device_error()
+    finally:
+        bs.bshuffle_set_pass_timing(False)
+        bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
+    return y, passes
+
+
+@pytest.mark.parametrize("width", [4, 8, 16])
+def test_ranked_form_runs_for_other_lengths(bs, width):
+    # lengths just above and below powers of two, ragged last chunks, one
+    # element short of the domain, and rounds other than the default
+    for n, seed, rounds in ((4097, 1, 24), (6000, 2, 24), (65535, 3, 24), (100_003, 4, 24), (2**20 + 1, 5, 24),
+                            (3 * 2**20 - 7, 6, 24), (2**22 - 1, 7, 24), (1_000_003, 8, 0), (1_000_003, 9, 1),
+                            (1_000_003, 10, 23)):
+        x = workloads.sweep_payload(n, width, seed)
+        y, passes = _passes(bs, to_device(x), seed, bs.BSHUFFLE_STRATEGY_STAGED, rounds)
+        assert passes == 2, n
+        assert np.array_equal(to_host(y, x), oracle.permute(x, seed, rounds)), (n, seed, rounds)
+
+
+@pytest.mark.parametrize("n,width", [(2**29 + 3, 4), (2**30 + 5, 4), (2**28 + 12345, 16)])
+def test_ranked_form_spans_over_several_ctas(bs, n, width):
+    # on 2^30- and 2^31-index domains the 512 spans of 2^21 or 2^22 indices
+    # are ranked by clusters of 2 or 4 CTAs; 16-byte elements at 2^28 + 12345
+    # take 4,096-element pass-1 chunks
+    seed = 11
+    x = workloads.sweep_payload(n, width, seed) if width == 16 else None
+    xd = to_device(x) if x is not None else torch.arange(n, dtype=torch.int32, device="cuda")
+    y, passes = _passes(bs, xd, seed, bs.BSHUFFLE_STRATEGY_STAGED)
+    assert passes == 2
+    idx = torch.from_numpy(oracle.indices_mt(n, seed).view(np.int64)).cuda()
+    assert torch.equal(y, xd[idx]), n
+    del y, idx, xd
+
+
 @pytest.mark.parametrize("rounds", [0, 1, 24])
 def test_staged_rounds(bs, rounds):
     x = workloads.uniform_u64(2**18, rounds)
@@ -52,7 +97,7 @@ def test_staged_rounds(bs, rounds):
 
 
 def test_staged_equals_single_pass_and_oracle_large(bs):
-    for n, width in ((2**25, 8), (2**26, 4), (2**24, 16)):
+    for n, width in ((2**25, 8), (2**26, 4), (2**24, 16), (2**25 + 1, 8), (2**26 + 999, 4), (2**24 + 3, 16)):
         x = workloads.sweep_payload(n, width, 9)
         xd = to_device(x)
         outs = []
@@ -62,7 +107,8 @@ def test_staged_equals_single_pass_and_oracle_large(bs):
             assert_no_device_error()
         bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
         assert torch.equal(outs[0], outs[1]), (n, width)
-        # every slot against the oracle (64 windows at 2^25 uint64 and 2^26 uint32)
+        # every slot against the oracle (64 windows at 2^25 uint64 and 2^26
+        # uint32; 256 spans of domain indices at the other lengths)
         idx = torch.from_numpy(oracle.indices_mt(n, 9).view(np.int64)).cuda()
         assert torch.equal(outs[0], xd[idx]), (n, width)
 
