@@ -266,7 +266,7 @@ def traffic_for(kernel: str, fingerprint: str):
 #   / (FMA-heavy thread instructions per evaluation, counted by ncu as
 #      smsp__inst_executed_pipe_fmaheavy.sum x 32 / evaluations).
 SMS, SMSP_PER_SM, FMAHEAVY_LANES, SM_HZ = 152, 4, 16, 2.07e9
-FMAHEAVY_INST_PER_INVERSE_EVAL = 72.0
+FMAHEAVY_INST_PER_INVERSE_EVAL = 80.1  # ncu, n = 2^26 uint64: 72 multiplies + 8 of addressing
 
 
 def alu_peak_evals_per_s() -> float:
