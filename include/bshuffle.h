@@ -145,6 +145,42 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
                      void *stream);
 
 /*
+ * One shuffle split by domain range, for running its parts on several
+ * devices (or one after another).  Algorithm 1 (Sec. 4) has one dependency
+ * between its indices, the exclusive scan of the keep flags; split the domain
+ * [0, 2^k) into consecutive ranges [first, end), and the kept indices of a
+ * range fill a contiguous run of output slots that starts at the number of
+ * kept indices in the ranges before it.  So:
+ *   1. each part calls bshuffle_count_range for its range (or for every
+ *      range: the count reads no data, so parts can also recompute the
+ *      counts of their predecessors instead of exchanging them);
+ *   2. the counts are scanned in range order (an all-gather of one integer
+ *      per part, then an exclusive sum): part r's first slot is offset_r;
+ *   3. each part calls bshuffle_permute_range with out pointing at slot
+ *      offset_r of the whole output (or at a buffer of count_r elements it
+ *      owns), reading the whole input (replicated, or reachable).
+ * The parts together write exactly bshuffle_permute(in, out, n, ...).
+ *
+ * bshuffle_count_range: *d_count (one uint64 in DEVICE memory, 8-byte
+ *   aligned, caller-owned) = the number of i in [first, end) with f(i) < n,
+ *   on the domain of n (end is clipped to 2^k).  The count is written
+ *   asynchronously on `stream` (it is zeroed first, then the GPU adds to it).
+ *   BSHUFFLE_ERR_INVALID if first > end.  No workspace.
+ * bshuffle_permute_range: out[t] = in[f(i_t)] for the t-th kept domain index
+ *   i_t in [first, end), in increasing order (t < the count above).  in holds
+ *   all n elements; out holds out_capacity elements (the range's count, from
+ *   bshuffle_count_range; 0 makes the call a no-op) and must not overlap in.
+ *   A slot at or past out_capacity is not written and records
+ *   BSHUFFLE_ERR_DEVICE_BOUNDS.  elem_bytes 1, 2, 4, 8 or 16; first < 2^32.
+ *   Uses the stream's workspace (one status word per 2,048 indices of the
+ *   range) and the fused single pass; errors as for bshuffle_permute.
+ */
+int bshuffle_count_range(uint64_t n, uint64_t seed, uint32_t rounds, uint64_t first, uint64_t end,
+                         uint64_t *d_count, void *stream);
+int bshuffle_permute_range(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                           uint32_t rounds, uint64_t first, uint64_t end, uint64_t out_capacity, void *stream);
+
+/*
  * The shuffle with the linear congruential bijection of Sec. 3.1 in place of
  * VariablePhilox: Y[j] = X[f(i_j)] as in bshuffle_permute, with
  * f(i) = (a i + c) mod 2^k, a odd (so f is a bijection of [0, 2^k)).  The

@@ -24,7 +24,11 @@ from ._lib import (
     MAX_ROUNDS,
     BShuffleError,
     bshuffle_batched,
+    bshuffle_count_range,
+    bshuffle_cuda_error_name,
     bshuffle_debug_skip_publish,
+    bshuffle_last_cuda_error,
+    bshuffle_permute_range,
     bshuffle_domain_bits,
     bshuffle_get_error,
     bshuffle_indices,
@@ -69,6 +73,7 @@ __all__ = [
     "bshuffle_debug_skip_publish", "bshuffle_version", "error_string", "load",
     "bshuffle_mc_group_diff", "bshuffle_random_gather", "mc_group_diff", "mc_pvalue", "BShuffleRows", "shuffle_rows",
     "bshuffle_shapley_voting", "shapley_voting", "bshuffle_window_scatter",
+    "bshuffle_count_range", "bshuffle_permute_range", "bshuffle_last_cuda_error", "bshuffle_cuda_error_name",
 ]
 
 

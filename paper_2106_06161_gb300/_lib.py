@@ -65,6 +65,8 @@ SIGNATURES = {
     "bshuffle_tuning_select": (_int, [_u32, _int]),
     "bshuffle_tuning_selected": (_int, [_u32]),
     "bshuffle_permute_lcg": (_int, [_p, _p, _u64, _u32, _u64, _p]),
+    "bshuffle_count_range": (_int, [_u64, _u64, _u32, _u64, _u64, _p, _p]),
+    "bshuffle_permute_range": (_int, [_p, _p, _u64, _u32, _u64, _u32, _u64, _u64, _u64, _p]),
     "bshuffle_lcg_params": (_int, [_u64, _u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "bshuffle_permute_ablation": (_int, [_p, _p, _u64, _u32, _u64, _u32, _int, _p]),
     "bshuffle_kendall_pairs": (_int, [_p, _u32, _u64, _p, _p]),
@@ -240,6 +242,18 @@ def bshuffle_tuning_selected(elem_bytes: int) -> int:
 def bshuffle_permute_lcg(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, seed: int, stream: int = 0) -> None:
     _check(load().bshuffle_permute_lcg(in_ptr, out_ptr, n, elem_bytes, seed & (2**64 - 1), stream),
            "bshuffle_permute_lcg")
+
+
+def bshuffle_count_range(n: int, seed: int, rounds: int, first: int, end: int, count_ptr: int,
+                         stream: int = 0) -> None:
+    _check(load().bshuffle_count_range(n, seed & (2**64 - 1), rounds, first, end, count_ptr, stream),
+           "bshuffle_count_range")
+
+
+def bshuffle_permute_range(in_ptr: int, out_ptr: int, n: int, elem_bytes: int, seed: int, rounds: int,
+                           first: int, end: int, out_capacity: int, stream: int = 0) -> None:
+    _check(load().bshuffle_permute_range(in_ptr, out_ptr, n, elem_bytes, seed & (2**64 - 1), rounds, first, end,
+                                         out_capacity, stream), "bshuffle_permute_range")
 
 
 def bshuffle_lcg_params(seed: int, n: int) -> tuple[int, int]:

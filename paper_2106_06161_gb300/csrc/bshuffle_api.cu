@@ -593,6 +593,73 @@ int bshuffle_permute_ablation(const void *in, void *out, uint64_t n, uint32_t el
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 
+int bshuffle_count_range(uint64_t n, uint64_t seed, uint32_t rounds, uint64_t first, uint64_t end,
+                         uint64_t *d_count, void *stream_ptr)
+{
+    int rc = check_common(n, rounds);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (d_count == nullptr) return BSHUFFLE_ERR_NULL;
+    if (reinterpret_cast<uintptr_t>(d_count) % alignof(uint64_t) != 0) return BSHUFFLE_ERR_ALIGN;
+    if (first > end) return BSHUFFLE_ERR_INVALID;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (n == 0) return BSHUFFLE_OK;
+    const Geometry g = geometry_of(n);
+    if (end > g.domain) end = g.domain;
+    if (first >= end) return BSHUFFLE_OK;
+    uint32_t keys[BSHUFFLE_MAX_ROUNDS];
+    fill_keys(seed, rounds, keys);
+    e = bsh::launch_count_range(g, keys, rounds, first, end, reinterpret_cast<unsigned long long *>(d_count),
+                                stream);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
+int bshuffle_permute_range(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                           uint32_t rounds, uint64_t first, uint64_t end, uint64_t out_capacity, void *stream_ptr)
+{
+    int rc = check_common(n, rounds);
+    if (rc != BSHUFFLE_OK) return rc;
+    if (elem_bytes != 1 && elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16)
+        return BSHUFFLE_ERR_ELEM;
+    if (first > end) return BSHUFFLE_ERR_INVALID;
+    if (n == 0) return BSHUFFLE_OK;
+    const Geometry g = geometry_of(n);
+    if (end > g.domain) end = g.domain;
+    if (first >= end) return BSHUFFLE_OK;
+    if (in == nullptr || out == nullptr) return BSHUFFLE_ERR_NULL;
+    const uint32_t al = align_of(elem_bytes);
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(in), b0 = reinterpret_cast<uintptr_t>(out);
+    if (a0 % al != 0 || b0 % al != 0) return BSHUFFLE_ERR_ALIGN;
+    if (out_capacity == 0) return BSHUFFLE_OK;
+    if (out_capacity > n) out_capacity = n;
+    if (a0 < b0 + out_capacity * elem_bytes && b0 < a0 + n * elem_bytes) return BSHUFFLE_ERR_ALIAS;
+
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    TileArgs a{};
+    a.in = in;
+    a.out = out;
+    a.g = g;
+    a.rounds = rounds;
+    a.elem_bytes = elem_bytes;
+    a.range_first = static_cast<uint32_t>(first);
+    a.range_end = end;
+    a.range_cap = out_capacity;
+    a.skip_publish_tile = g_skip_publish.load();
+    a.timeout_ns = g_timeout_ns.load();
+    fill_keys(seed, rounds, a.keys);
+    const uint64_t tile = bsh::elem_tile_size(0);
+    const uint64_t tiles = (end - first + tile - 1) / tile;
+    a.num_tiles = static_cast<uint32_t>(tiles);
+    Workspace *ws = nullptr;
+    rc = acquire_workspace(stream, tiles, &ws);
+    if (rc != BSHUFFLE_OK) return rc;
+    a.ws = ws->header();
+    a.status = ws->status();
+    const cudaError_t e = bsh::launch_permute_range(a, elem_bytes, stream);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+}
+
 int bshuffle_lcg_params(uint64_t seed, uint64_t n, uint64_t *a, uint64_t *c)
 {
     if (a == nullptr || c == nullptr) return BSHUFFLE_ERR_NULL;

@@ -45,7 +45,9 @@ struct TileArgs {
     uint32_t rounds;
     uint32_t num_tiles;
     uint32_t elem_bytes;        // element width for the row kernels
-    uint32_t pad0;
+    uint32_t range_first;       // range launches: first domain index of the range
+    uint64_t range_end;         // range launches: one past the last domain index
+    uint64_t range_cap;         // range launches: elements the output holds
     int64_t skip_publish_tile;  // test hook, -1 = off
     uint64_t timeout_ns;        // look-back wait limit
     WsHeader *ws;
@@ -90,6 +92,13 @@ cudaError_t launch_elem(const TileArgs &a, Mode mode, uint32_t elem_bytes, int c
 cudaError_t launch_gather_tuned(const TileArgs &a, uint32_t elem_bytes, int config, cudaStream_t stream);
 // The fused gather with the LCG bijection (default configuration).
 cudaError_t launch_gather_lcg(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream);
+// Algorithm 1 restricted to the domain range [range_first, range_end): the
+// gather of the range's kept indices into out[0 .. count) (num_tiles tiles of
+// elem_tile_size(0) indices from range_first), and the count alone (added to
+// *count, which the caller zeroes).  elem_bytes 1, 2, 4, 8 or 16.
+cudaError_t launch_permute_range(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream);
+cudaError_t launch_count_range(const Geometry &g, const uint32_t *keys, uint32_t rounds, uint64_t first,
+                               uint64_t end, unsigned long long *count, cudaStream_t stream);
 cudaError_t launch_rows(const TileArgs &a, Mode mode, cudaStream_t stream);
 // Power-of-two lengths (g.n == g.domain >= 16): Algorithm 1 without its scan,
 // which is the identity when nothing is dropped.  Every mode; elem_bytes 1,

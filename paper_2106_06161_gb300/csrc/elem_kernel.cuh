@@ -19,7 +19,10 @@
 // ROUNDS = 0 reads the round count at run time; ROUNDS > 0 unrolls exactly
 // that many rounds (valid only for calls with rounds == ROUNDS).  BIJ selects
 // the bijection: VariablePhilox (Sec. 3.2) or the LCG of Sec. 3.1,
-// b = (a i + c) mod 2^k with a odd.
+// b = (a i + c) mod 2^k with a odd.  RANGE restricts the launch to the domain
+// indices [range_first, range_end) (tiles counted from range_first), whose
+// kept elements fill out[0 .. count): one part of a shuffle split by domain
+// range.
 #pragma once
 
 #include <cstdint>
@@ -40,7 +43,7 @@ __device__ __forceinline__ T load_nc(const T *p)
     return __ldg(p);
 }
 
-template <class T, Mode MODE, bool ODD, int BLOCK, int ITEMS, int ROUNDS, int BIJ = kVarPhilox>
+template <class T, Mode MODE, bool ODD, int BLOCK, int ITEMS, int ROUNDS, int BIJ = kVarPhilox, bool RANGE = false>
 __global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant__ TileArgs a)
 {
     constexpr int WARPS = BLOCK / 32;
@@ -63,7 +66,7 @@ __global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant_
         }
         return;
     }
-    const uint32_t base = tile * static_cast<uint32_t>(BLOCK * ITEMS);
+    const uint32_t base = (RANGE ? a.range_first : 0u) + tile * static_cast<uint32_t>(BLOCK * ITEMS);
 
     // 1. bijection
     uint32_t left[ITEMS], right[ITEMS];
@@ -91,7 +94,13 @@ __global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant_
         } else {
             src[j] = (left[j] << a.g.R) | right[j];
         }
-        keep[j] = static_cast<uint64_t>(i) < a.g.domain && src[j] < a.g.n;
+        if constexpr (RANGE) {  // 64-bit: the last tile of a range may pass 2^32
+            const uint64_t i64 = uint64_t{a.range_first} + uint64_t{tile} * (BLOCK * ITEMS) +
+                                 static_cast<uint64_t>(j * BLOCK) + threadIdx.x;
+            keep[j] = i64 < a.range_end && src[j] < a.g.n;
+        } else {
+            keep[j] = static_cast<uint64_t>(i) < a.g.domain && src[j] < a.g.n;
+        }
     }
 
     // 2. random reads issued before the scan
@@ -122,11 +131,15 @@ __global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant_
     // 4. compacted output
     if (ok) {
         const uint32_t lt = dev::lanemask_lt();
+        // a range's slots end at the caller's output capacity
+        uint32_t limit = a.g.n;
+        if constexpr (RANGE)
+            if (a.range_cap < limit) limit = static_cast<uint32_t>(a.range_cap);
         uint32_t dst[ITEMS];
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             dst[j] = prefix + st.counts[j * WARPS + warp] + __popc(mask[j] & lt);
-            if (keep[j] && dst[j] >= a.g.n) {
+            if (keep[j] && dst[j] >= limit) {
                 dev::record_error(a.ws, dev::kErrDeviceBounds, dst[j]);
                 keep[j] = false;
             }
