@@ -346,10 +346,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     bs.bshuffle_set_strategy(STRATEGIES[args.strategy])
-    # the library's autotuner picks the single-pass configuration per width
-    # (used for lengths that are not powers of two); a few seconds
+    # the library's autotuner picks, per width, the shapes of the plain and
+    # pipelined single passes and of the batched kernel (4 and 8 bytes: the
+    # widths the bench runs them at); a few seconds
     from paper_2106_06161_gb300 import autotune
-    tuning = autotune.tune(widths=(ELEM,), n=2**26 + 1, reps=3, warmup=1, save=False)
+    tuning = autotune.tune(widths=(4, ELEM), reps=3, warmup=1, save=False)
 
     seed = SEED + rank
     host = workloads.uniform_u64(N_MAIN, seed)
@@ -421,7 +422,7 @@ def run_ours(args):
             "logical_gbps": 2 * N_MAIN * ELEM / (ms_per_step * 1e-3) / 1e9,
             "strategy": {0: "auto", 1: "single_pass", 2: "staged", 3: "pipelined"}[bs.bshuffle_get_strategy()],
             "kernels_per_step": len(passes), "passes": pass_lines,
-            "single_pass_tuning": tuning, "extra": extra,
+            "tuning": tuning, "extra": extra,
             "e2e": e2e, "gpu_launches": args.steps * len(passes), "clocks": clk,
             "cpu_baseline": cpu, "roofline": roofline,
         }
@@ -746,6 +747,17 @@ def secondary(bs, torch, dev, stream):
         for t in range(count):
             bs.bshuffle_permute(ins[t], outs[t], ns[t], 4, t, ROUNDS, sptr)
 
+    # the batched kernel's default shape against the autotuner's choice
+    from paper_2106_06161_gb300 import _lib as L
+    tuned = L.bshuffle_kernel_selected(L.BSHUFFLE_KERNEL_BATCHED, 4)
+    by_config = {}
+    for config in sorted({0, tuned}):
+        L.bshuffle_kernel_select(L.BSHUFFLE_KERNEL_BATCHED, 4, config)
+        for _ in range(3):
+            fb()
+        _, tcfg = timed_launches(fb, 10, stream, torch)
+        by_config[config] = tcfg / 10
+    L.bshuffle_kernel_select(L.BSHUFFLE_KERNEL_BATCHED, 4, tuned)
     for _ in range(3):
         fb()
     _, tb = timed_launches(fb, 10, stream, torch)
@@ -757,7 +769,9 @@ def secondary(bs, torch, dev, stream):
     out["batched_4096_uneven_int32"] = {
         "batched_ms": tb / 10, "plain_ms": tp / 3, "speedup": (tp / 3) / (tb / 10),
         "batched_shuffles_per_s": count / (tb / 10 * 1e-3), "plain_shuffles_per_s": count / (tp / 3 * 1e-3),
-        "total_elements": int(sizes.sum()), "batched_equals_plain": same}
+        "total_elements": int(sizes.sum()), "batched_equals_plain": same,
+        "batched_ms_default_shape": by_config[0], "batched_ms_tuned_shape": by_config[tuned],
+        "tuned_config": tuned}
     return out
 
 

@@ -399,6 +399,32 @@ int bshuffle_tuning_select(uint32_t elem_bytes, int config);
 int bshuffle_tuning_selected(uint32_t elem_bytes);
 
 /*
+ * Tuning of the three kernels the default strategy runs for shuffles without
+ * staging: `kernel` is BSHUFFLE_KERNEL_SINGLE_PASS (the plain fused kernel:
+ * small domains, and every call under BSHUFFLE_STRATEGY_SINGLE_PASS; its
+ * configurations are those of bshuffle_tuning_*), BSHUFFLE_KERNEL_PIPELINED
+ * (the pipelined single pass of bshuffle_permute for 4-, 8- and 16-byte
+ * elements) or BSHUFFLE_KERNEL_BATCHED (the persistent kernel of
+ * bshuffle_batched for 4-, 8- and 16-byte elements).  Configuration c has
+ * `threads` per CTA (the pipelined shapes: compute warps plus one look-back
+ * warp), `items` domain indices per compute thread, the resident CTAs per SM
+ * its register budget targets (0: not set) and the rounds unrolled at compile
+ * time (24: the default count runs unrolled, other counts in a loop; 0: every
+ * count runs in a loop).  Configuration 0 is the default.  Every
+ * configuration computes the same output; the choice is process-wide per
+ * element width and changes speed only.  Select and selected return
+ * BSHUFFLE_ERR_INVALID for another kernel, width or configuration.
+ */
+#define BSHUFFLE_KERNEL_SINGLE_PASS 0
+#define BSHUFFLE_KERNEL_PIPELINED 1
+#define BSHUFFLE_KERNEL_BATCHED 2
+int bshuffle_kernel_configs(int kernel);
+int bshuffle_kernel_describe(int kernel, int config, int *threads, int *items, int *ctas_per_sm,
+                             int *rounds_unrolled);
+int bshuffle_kernel_select(int kernel, uint32_t elem_bytes, int config);
+int bshuffle_kernel_selected(int kernel, uint32_t elem_bytes);
+
+/*
  * Per-pass timing (tracing aid, off by default).  While on, bshuffle_permute
  * records CUDA events around each of its kernels on the caller's stream.
  * bshuffle_last_pass_ms synchronises `stream` and writes the durations of the

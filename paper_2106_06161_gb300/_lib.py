@@ -29,6 +29,9 @@ BSHUFFLE_STRATEGY_AUTO = 0
 BSHUFFLE_STRATEGY_SINGLE_PASS = 1
 BSHUFFLE_STRATEGY_STAGED = 2
 BSHUFFLE_STRATEGY_PIPELINED = 3
+BSHUFFLE_KERNEL_SINGLE_PASS = 0
+BSHUFFLE_KERNEL_PIPELINED = 1
+BSHUFFLE_KERNEL_BATCHED = 2
 DEFAULT_ROUNDS = 24
 MAX_ROUNDS = 64
 MAX_N = 2**32 - 1
@@ -64,6 +67,11 @@ SIGNATURES = {
     "bshuffle_tuning_describe": (_int, [_int, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "bshuffle_tuning_select": (_int, [_u32, _int]),
     "bshuffle_tuning_selected": (_int, [_u32]),
+    "bshuffle_kernel_configs": (_int, [_int]),
+    "bshuffle_kernel_describe": (_int, [_int, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                        ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "bshuffle_kernel_select": (_int, [_int, _u32, _int]),
+    "bshuffle_kernel_selected": (_int, [_int, _u32]),
     "bshuffle_permute_lcg": (_int, [_p, _p, _u64, _u32, _u64, _p]),
     "bshuffle_count_range": (_int, [_u64, _u64, _u32, _u64, _u64, _p, _p]),
     "bshuffle_permute_range": (_int, [_p, _p, _u64, _u32, _u64, _u32, _u64, _u64, _u64, _p]),
@@ -229,6 +237,27 @@ def bshuffle_tuning_configs() -> list[dict]:
                "bshuffle_tuning_describe")
         out.append({"config": c, "block": b.value, "items": i.value, "rounds_unrolled": r.value})
     return out
+
+
+def bshuffle_kernel_configs(kernel: int) -> list[dict]:
+    """Every configuration of a tunable kernel (BSHUFFLE_KERNEL_*)."""
+    count = _check(load().bshuffle_kernel_configs(kernel), "bshuffle_kernel_configs")
+    out = []
+    for c in range(count):
+        t, i, m, r = _int(0), _int(0), _int(0), _int(0)
+        _check(load().bshuffle_kernel_describe(kernel, c, ctypes.byref(t), ctypes.byref(i), ctypes.byref(m),
+                                               ctypes.byref(r)), "bshuffle_kernel_describe")
+        out.append({"config": c, "threads": t.value, "items": i.value, "ctas_per_sm": m.value,
+                    "rounds_unrolled": r.value})
+    return out
+
+
+def bshuffle_kernel_select(kernel: int, elem_bytes: int, config: int) -> None:
+    _check(load().bshuffle_kernel_select(kernel, elem_bytes, config), "bshuffle_kernel_select")
+
+
+def bshuffle_kernel_selected(kernel: int, elem_bytes: int) -> int:
+    return _check(load().bshuffle_kernel_selected(kernel, elem_bytes), "bshuffle_kernel_selected")
 
 
 def bshuffle_tuning_select(elem_bytes: int, config: int) -> None:

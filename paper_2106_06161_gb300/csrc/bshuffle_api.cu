@@ -277,7 +277,10 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
                         (strategy == BSHUFFLE_STRATEGY_PIPELINED ||
                          (strategy == BSHUFFLE_STRATEGY_AUTO && pipe_by_default))));
     const int config = rows ? 0 : bsh::elem_config_for(elem_bytes, mode, rounds);
-    const uint64_t tile = rows ? bsh::rows_tile_size(elem_bytes) : (pipe ? bsh::pipe_tile_size(elem_bytes) : bsh::elem_tile_size(config));
+    const int pipe_config = pipe ? bsh::pipe_config_for(elem_bytes, mode) : 0;
+    const uint64_t tile = rows   ? bsh::rows_tile_size(elem_bytes)
+                          : pipe ? bsh::pipe_tile_size(elem_bytes, pipe_config)
+                                 : bsh::elem_tile_size(config);
     const uint64_t tiles = (a.g.domain + tile - 1) / tile;
     a.num_tiles = static_cast<uint32_t>(tiles);
     Workspace *ws = nullptr;
@@ -288,7 +291,7 @@ int run_fused(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64
     cudaEvent_t *marks = mode == Mode::Gather ? timing_marks(ws) : nullptr;
     if (marks != nullptr && cudaEventRecord(marks[0], stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
     const cudaError_t e = rows   ? bsh::launch_rows(a, mode, stream)
-                          : pipe ? bsh::launch_pipe(a, mode, elem_bytes, stream)
+                          : pipe ? bsh::launch_pipe(a, mode, elem_bytes, pipe_config, stream)
                                  : bsh::launch_elem(a, mode, elem_bytes, config, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     if (marks != nullptr) {
@@ -913,6 +916,61 @@ int bshuffle_tuning_select(uint32_t elem_bytes, int config)
 }
 
 int bshuffle_tuning_selected(uint32_t elem_bytes) { return bsh::selected_elem_config(elem_bytes); }
+
+int bshuffle_kernel_configs(int kernel)
+{
+    switch (kernel) {
+    case BSHUFFLE_KERNEL_SINGLE_PASS: return bsh::kNumElemConfigs;
+    case BSHUFFLE_KERNEL_PIPELINED: return bsh::kNumPipeConfigs;
+    case BSHUFFLE_KERNEL_BATCHED: return bsh::kNumBatchConfigs;
+    default: return BSHUFFLE_ERR_INVALID;
+    }
+}
+
+int bshuffle_kernel_describe(int kernel, int config, int *threads, int *items, int *ctas_per_sm,
+                             int *rounds_unrolled)
+{
+    const int count = bshuffle_kernel_configs(kernel);
+    if (count < 0 || config < 0 || config >= count) return BSHUFFLE_ERR_INVALID;
+    if (threads == nullptr || items == nullptr || ctas_per_sm == nullptr || rounds_unrolled == nullptr)
+        return BSHUFFLE_ERR_NULL;
+    if (kernel == BSHUFFLE_KERNEL_SINGLE_PASS) {
+        *threads = bsh::kElemConfigs[config].block;
+        *items = bsh::kElemConfigs[config].items;
+        *ctas_per_sm = 0;
+        *rounds_unrolled = bsh::kElemConfigs[config].rounds;
+        return BSHUFFLE_OK;
+    }
+    const bsh::PipeConfig &c =
+        kernel == BSHUFFLE_KERNEL_PIPELINED ? bsh::kPipeConfigs[config] : bsh::kBatchConfigs[config];
+    *threads = (c.warps + 1) * 32;
+    *items = c.items;
+    *ctas_per_sm = c.ctas_per_sm;
+    *rounds_unrolled = c.unroll != 0 ? static_cast<int>(BSHUFFLE_DEFAULT_ROUNDS) : 0;
+    return BSHUFFLE_OK;
+}
+
+int bshuffle_kernel_select(int kernel, uint32_t elem_bytes, int config)
+{
+    int rc = -1;
+    switch (kernel) {
+    case BSHUFFLE_KERNEL_SINGLE_PASS: rc = bsh::select_elem_config(elem_bytes, config); break;
+    case BSHUFFLE_KERNEL_PIPELINED: rc = bsh::select_pipe_config(elem_bytes, config); break;
+    case BSHUFFLE_KERNEL_BATCHED: rc = bsh::select_batch_config(elem_bytes, config); break;
+    default: break;
+    }
+    return rc == 0 ? BSHUFFLE_OK : BSHUFFLE_ERR_INVALID;
+}
+
+int bshuffle_kernel_selected(int kernel, uint32_t elem_bytes)
+{
+    switch (kernel) {
+    case BSHUFFLE_KERNEL_SINGLE_PASS: return bsh::selected_elem_config(elem_bytes);
+    case BSHUFFLE_KERNEL_PIPELINED: return bsh::selected_pipe_config(elem_bytes);
+    case BSHUFFLE_KERNEL_BATCHED: return bsh::selected_batch_config(elem_bytes);
+    default: return BSHUFFLE_ERR_INVALID;
+    }
+}
 
 int bshuffle_set_pass_timing(int on)
 {

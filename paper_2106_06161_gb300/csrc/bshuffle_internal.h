@@ -64,6 +64,16 @@ enum class Mode : int {
     Index64 = 3,  // out[j] = (uint64) f(i_j)
 };
 
+// Shape of a persistent pipelined kernel: compute warps, domain indices per
+// compute thread, resident CTAs per SM its register budget targets, and
+// whether the default round count runs fully unrolled (1) or in a loop (0).
+struct PipeConfig {
+    int warps;
+    int items;
+    int ctas_per_sm;
+    int unroll;
+};
+
 // Configurations of the element kernel: CTA size, items per thread, and
 // rounds unrolled at compile time (0 = read at run time).  Configuration 0
 // is the default and is instantiated for every mode and width; the others
@@ -130,6 +140,8 @@ struct BatchArgs {
     uint32_t rounds;
     uint32_t elem_bytes;
     uint32_t grid;          // CTAs of the persistent kernel
+    uint32_t tile;          // domain indices per tile of the persistent kernel's shape
+    uint32_t pad0;
     uint64_t timeout_ns;
     int64_t skip_publish_tile;
     WsHeader *ws;
@@ -137,7 +149,13 @@ struct BatchArgs {
     uint64_t *total_tiles;  // written by the planning kernel
 };
 
-uint32_t batch_tile_size(uint32_t elem_bytes);
+// Shapes of the pipelined persistent kernel (4-, 8- and 16-byte elements):
+// compute warps, items per compute thread, resident CTAs per SM targeted,
+// default rounds unrolled; the shape selected per width.
+constexpr int kNumBatchConfigs = 6;
+extern const PipeConfig kBatchConfigs[kNumBatchConfigs];
+int select_batch_config(uint32_t elem_bytes, int config);
+int selected_batch_config(uint32_t elem_bytes);
 uint64_t batch_ring_words();
 // Enqueue the planning kernel and the persistent kernel (elem_bytes 1..16).
 cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream);
@@ -226,10 +244,19 @@ struct McArgs {
 
 cudaError_t launch_mc(const McArgs &a, cudaStream_t stream);
 
-// Pipelined single pass: which calls it serves, its tile size, and launch.
+// Pipelined single pass: which calls it serves, its shapes (compute warps,
+// items per compute thread, resident CTAs per SM targeted, default rounds
+// unrolled), the shape selected per width (gathers of 4, 8 and 16 bytes; 0
+// for every other call), its tile size, and launch.
+constexpr int kNumPipeConfigs = 6;
+extern const PipeConfig kPipeConfigs[kNumPipeConfigs];
+int pipe_config_for(uint32_t elem_bytes, Mode mode);
+int select_pipe_config(uint32_t elem_bytes, int config);
+int selected_pipe_config(uint32_t elem_bytes);
 bool pipe_supports(Mode mode, uint32_t elem_bytes);
-uint32_t pipe_tile_size(uint32_t elem_bytes);
-cudaError_t launch_pipe(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream);
+uint32_t pipe_tile_size(uint32_t elem_bytes, int config);
+cudaError_t launch_pipe(const TileArgs &a, Mode mode, uint32_t elem_bytes, int config, cudaStream_t stream);
+cudaError_t launch_pipe_tuned(const TileArgs &a, uint32_t elem_bytes, int config, cudaStream_t stream);
 
 struct ShapleyArgs {
     const uint32_t *w;  // player weights

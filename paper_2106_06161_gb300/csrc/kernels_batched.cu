@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(const __grid_c
             }
         }
         if (bad) k = 0;
-        const uint64_t tiles = k == 0 ? 0 : ((uint64_t{1} << k) + kTile - 1) / kTile;
+        const uint64_t tiles = k == 0 ? 0 : ((uint64_t{1} << k) + a.tile - 1) / a.tile;
         a.plan[t].k = k;
         a.plan[t].tiles = static_cast<uint32_t>(tiles);
         sum += tiles;
@@ -333,12 +333,11 @@ __global__ void __launch_bounds__(kBBlock, min_ctas_for(sizeof(T))) batch_tile_k
 // warp 0 takes the next ticket and resolves its instance.  Tickets are taken
 // only when the CTA no longer waits on other tiles, and aggregates never wait
 // on a look-back.  Used for 4-, 8- and 16-byte elements.
-constexpr int kPipeWarps = 8;
-constexpr int kPipeItems = kTile / (kPipeWarps * 32);
-static_assert(kPipeItems * kPipeWarps * 32 == static_cast<int>(kTile), "tile shape");
-
+// Shapes (kBatchConfigs): NW compute warps of ITEMS indices per thread, MINB
+// resident CTAs per SM targeted, UNROLL the default 24 rounds unrolled.
+// Shape 0 (8 x 8, 3 CTAs per SM) is the default.
+template <int E>
 struct BatchPipeShared {
-    static constexpr int E = kPipeWarps * kPipeItems;
     uint64_t full[2];            // compute -> look-back: ballots of the buffer's tile written
     uint64_t ranked[2];          // look-back -> compute: offsets and prefix ready
     unsigned long long aggc[2];  // (compute warps done << 32) | kept count
@@ -351,14 +350,17 @@ struct BatchPipeShared {
     uint32_t abort;
 };
 
-template <class T>
-__global__ void __launch_bounds__((kPipeWarps + 1) * 32, 3) batch_pipe_kernel(const __grid_constant__ BatchArgs a)
+template <class T, int NW, int ITEMS, int MINB, bool UNROLL>
+__global__ void __launch_bounds__((NW + 1) * 32, MINB) batch_pipe_kernel(const __grid_constant__ BatchArgs a)
 {
+    constexpr int kPipeWarps = NW;
+    constexpr int kPipeItems = ITEMS;
+    constexpr uint32_t kPTile = NW * 32 * ITEMS;
     constexpr uint32_t NCT = kPipeWarps * 32;
-    constexpr int E = BatchPipeShared::E;
-    __shared__ BatchPipeShared sh;
+    constexpr int E = NW * ITEMS;
+    __shared__ BatchPipeShared<E> sh;
     extern __shared__ __align__(16) unsigned char batch_dyn[];
-    T *vals = reinterpret_cast<T *>(batch_dyn);  // [2][kTile]
+    T *vals = reinterpret_cast<T *>(batch_dyn);  // [2][kPTile]
     const dev::StatusRing ring{a.status, kRingWords - 1, kRingShift, 1u};
     const uint64_t total = *reinterpret_cast<volatile const uint64_t *>(a.total_tiles);
     const uint32_t lane = threadIdx.x & 31u;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__((kPipeWarps + 1) * 32, 3) batch_pipe_kernel(co
             const bool stop = tile >= total;
             if (!stop) {
                 const Geometry &g = job.g;
-                const uint32_t base = (tile - static_cast<uint32_t>(job.first)) * kTile;
+                const uint32_t base = (tile - static_cast<uint32_t>(job.first)) * kPTile;
                 uint32_t left[kPipeItems], right[kPipeItems];
 #pragma unroll
                 for (int j = 0; j < kPipeItems; ++j) {
@@ -403,12 +405,19 @@ __global__ void __launch_bounds__((kPipeWarps + 1) * 32, 3) batch_pipe_kernel(co
                     left[j] = i >> g.R;
                     right[j] = i & g.rmask;
                 }
-                if (g.k & 1u)
-                    dev::cipher_items<true, kPipeItems>(left, right, sh.keys[b], a.rounds, g);
-                else
-                    dev::cipher_items<false, kPipeItems>(left, right, sh.keys[b], a.rounds, g);
+                if constexpr (UNROLL) {
+                    if (g.k & 1u)
+                        dev::cipher_items<true, kPipeItems>(left, right, sh.keys[b], a.rounds, g);
+                    else
+                        dev::cipher_items<false, kPipeItems>(left, right, sh.keys[b], a.rounds, g);
+                } else {
+                    if (g.k & 1u)
+                        dev::cipher_items_loop<true, kPipeItems>(left, right, sh.keys[b], a.rounds, g);
+                    else
+                        dev::cipher_items_loop<false, kPipeItems>(left, right, sh.keys[b], a.rounds, g);
+                }
                 const T *in = static_cast<const T *>(job.in);
-                T *buf = vals + static_cast<size_t>(b) * kTile;
+                T *buf = vals + static_cast<size_t>(b) * kPTile;
                 uint32_t count = 0;
 #pragma unroll
                 for (int j = 0; j < kPipeItems; ++j) {
@@ -442,7 +451,7 @@ __global__ void __launch_bounds__((kPipeWarps + 1) * 32, 3) batch_pipe_kernel(co
                 if (ct == 0 && !stop && *abort == 0u) next = atomicAdd(&a.ws->batch_ticket, 1u);
                 dev::cp_async_wait_prior();
                 if (ranked && sh.ok[pb] != 0u) {
-                    const T *pbuf = vals + static_cast<size_t>(pb) * kTile;
+                    const T *pbuf = vals + static_cast<size_t>(pb) * kPTile;
                     const uint32_t prefix = sh.prefix[pb];
 #pragma unroll
                     for (int j = 0; j < kPipeItems; ++j) {
@@ -530,11 +539,13 @@ __global__ void __launch_bounds__((kPipeWarps + 1) * 32, 3) batch_pipe_kernel(co
     }
 }
 
-template <class T>
+template <class T, int NW, int ITEMS, int MINB, bool UNROLL>
 cudaError_t launch_pipe_typed(const BatchArgs &a, cudaStream_t stream)
 {
-    constexpr int THREADS = (kPipeWarps + 1) * 32;
-    constexpr size_t DYN = 2 * sizeof(T) * kTile;
+    constexpr int THREADS = (NW + 1) * 32;
+    constexpr uint32_t TILE = NW * 32 * ITEMS;
+    constexpr size_t DYN = 2 * sizeof(T) * TILE;
+    const auto kernel = batch_pipe_kernel<T, NW, ITEMS, MINB, UNROLL>;
     static std::atomic<int> per_sm[64];  // CTAs to launch per device, 0 until first use
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
@@ -542,10 +553,10 @@ cudaError_t launch_pipe_typed(const BatchArgs &a, cudaStream_t stream)
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     int ctas_cached = per_sm[device].load(std::memory_order_acquire);
     if (ctas_cached == 0) {
-        e = cudaFuncSetAttribute(batch_pipe_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(DYN));
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(DYN));
         if (e != cudaSuccess) return e;
         int blocks = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_pipe_kernel<T>, THREADS, DYN);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, THREADS, DYN);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
@@ -554,10 +565,11 @@ cudaError_t launch_pipe_typed(const BatchArgs &a, cudaStream_t stream)
     }
     BatchArgs b = a;
     b.grid = static_cast<uint32_t>(ctas_cached);
+    b.tile = TILE;
     batch_plan_kernel<<<1, kPlanThreads, 0, stream>>>(b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    batch_pipe_kernel<T><<<b.grid, THREADS, DYN, stream>>>(b);
+    kernel<<<b.grid, THREADS, DYN, stream>>>(b);
     return cudaGetLastError();
 }
 
@@ -581,6 +593,7 @@ cudaError_t launch_typed(const BatchArgs &a, cudaStream_t stream)
     }
     BatchArgs b = a;
     b.grid = static_cast<uint32_t>(ctas_cached);
+    b.tile = kTile;
     batch_plan_kernel<<<1, kPlanThreads, 0, stream>>>(b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -588,19 +601,56 @@ cudaError_t launch_typed(const BatchArgs &a, cudaStream_t stream)
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_pipe_config(const BatchArgs &a, int config, cudaStream_t stream)
+{
+    static_assert(kNumBatchConfigs == 6, "shapes instantiated here");
+    switch (config) {
+    case 0: return launch_pipe_typed<T, 8, 8, 3, true>(a, stream);
+    case 1: return launch_pipe_typed<T, 8, 4, 4, true>(a, stream);
+    case 2: return launch_pipe_typed<T, 8, 16, 2, true>(a, stream);
+    case 3: return launch_pipe_typed<T, 4, 8, 5, true>(a, stream);
+    case 4: return launch_pipe_typed<T, 16, 4, 2, true>(a, stream);
+    case 5: return launch_pipe_typed<T, 8, 8, 3, false>(a, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+std::atomic<int> g_batch_selected[3];  // 4, 8, 16 bytes
+
+int batch_slot(uint32_t elem_bytes) { return elem_bytes == 4 ? 0 : elem_bytes == 8 ? 1 : elem_bytes == 16 ? 2 : -1; }
+
 }  // namespace
 
-uint32_t batch_tile_size(uint32_t) { return kTile; }
+const PipeConfig kBatchConfigs[kNumBatchConfigs] = {
+    {8, 8, 3, 1}, {8, 4, 4, 1}, {8, 16, 2, 1}, {4, 8, 5, 1}, {16, 4, 2, 1}, {8, 8, 3, 0},
+};
+
+int select_batch_config(uint32_t elem_bytes, int config)
+{
+    const int slot = batch_slot(elem_bytes);
+    if (slot < 0 || config < 0 || config >= kNumBatchConfigs) return -1;
+    g_batch_selected[slot].store(config);
+    return 0;
+}
+
+int selected_batch_config(uint32_t elem_bytes)
+{
+    const int slot = batch_slot(elem_bytes);
+    return slot < 0 ? 0 : g_batch_selected[slot].load();
+}
+
 uint64_t batch_ring_words() { return kRingWords; }
 
 cudaError_t launch_batched(const BatchArgs &a, cudaStream_t stream)
 {
+    const int config = selected_batch_config(a.elem_bytes);
     switch (a.elem_bytes) {
     case 1: return launch_typed<unsigned char>(a, stream);
     case 2: return launch_typed<unsigned short>(a, stream);
-    case 4: return launch_pipe_typed<unsigned int>(a, stream);
-    case 8: return launch_pipe_typed<unsigned long long>(a, stream);
-    case 16: return launch_pipe_typed<uint4>(a, stream);
+    case 4: return launch_pipe_config<unsigned int>(a, config, stream);
+    case 8: return launch_pipe_config<unsigned long long>(a, config, stream);
+    case 16: return launch_pipe_config<uint4>(a, config, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,301 +1,71 @@
-// Pipelined single pass of Algorithm 1 (gather and scatter of 4-, 8- and
-// 16-byte elements, and the index output): the same output as the fused tile
-// kernel, with the inter-tile look-back taken off the compute warps' path.
+// Pipelined single pass of Algorithm 1 (pipe_kernel.cuh): the default shape
+// for every mode and width, the table of shapes the gather of 4-, 8- and
+// 16-byte elements can be tuned over, and the selection per width.
 //
-// In the plain fused kernel every warp of a tile waits while one warp looks
-// back, and under a full load of random gathers a look-back takes several
-// L2 round trips.  Here a persistent CTA holds NCW compute warps and one
-// look-back warp, and the compute warps run one tile ahead of their stores:
-//
-//   compute warps, iteration i (buffer i % 2): take a ticket, evaluate the
-//     bijection, start copying the kept elements X[f(i)] into the buffer
-//     with cp.async (one copy group per thread and tile; the index and
-//     scatter modes store the image itself), store the keep ballots and
-//     publish the tile aggregate (the last compute warp to add its count
-//     does it); then store tile i - 1: wait for its rank (look-back warp)
-//     and for this thread's own copy group of that tile, and write each
-//     element this thread gathered to its slot (scatter: read the element of
-//     that slot and write it to the image).
-//   look-back warp, tile i: wait for the ballots, form the in-tile offsets,
-//     look back, publish the inclusive prefix and hand the prefix to the
-//     compute warps.
-//
-// Tickets stay in order of readiness: a tile's aggregate is published by the
-// compute warps right after its ballots, never after another tile's
-// look-back, and the compute warps wait for a rank only after that.  The
-// smallest unfinished ticket therefore always makes progress.  Every wait is
-// bounded.
+// Shape 0 is the default: eight compute warps of 8 items and three resident
+// CTAs per SM measured fastest on GB300 (more tiles in flight lengthen every
+// look-back walk; fewer warps hide less latency).  The other shapes are
+// instantiated in kernels_pipe_tuned.cu and serve bshuffle_permute only.
 #include <atomic>
 #include <cstdint>
-#include <type_traits>
 
-#include "bshuffle_device.cuh"
 #include "bshuffle_internal.h"
+#include "pipe_kernel.cuh"
 
 namespace bsh {
-namespace {
 
-using dev::kFull;
-
-// Shape of the persistent CTA (overridable at build time for tuning
-// experiments): compute warps, domain indices per compute thread for 16-byte
-// elements (others take 8), and the resident CTAs per SM that the register
-// budget targets.  Three CTAs per SM measured fastest: more tiles in flight
-// lengthen every look-back walk.
-#ifndef BSHUFFLE_PIPE_ITEMS16
-#define BSHUFFLE_PIPE_ITEMS16 8
-#endif
-#ifndef BSHUFFLE_PIPE_MIN_CTAS
-#define BSHUFFLE_PIPE_MIN_CTAS 3
-#endif
-constexpr int kPipeComputeWarps = 8;
-constexpr int pipe_items(uint32_t elem_bytes) { return elem_bytes >= 16 ? BSHUFFLE_PIPE_ITEMS16 : 8; }
-constexpr uint32_t pipe_tile(uint32_t elem_bytes) { return kPipeComputeWarps * 32 * pipe_items(elem_bytes); }
-
-template <int NCW, int ITEMS>
-struct PipeShared {
-    static constexpr int E = NCW * ITEMS;
-    uint64_t full[2];            // compute -> look-back: ballots of the buffer's tile written
-    uint64_t ranked[2];          // look-back -> compute: offsets and prefix of that tile ready
-    unsigned long long aggc[2];  // (compute warps done << 32) | kept count, per buffer
-    uint32_t masks[2][E];        // keep ballot per (item, compute warp)
-    uint32_t offs[2][E];         // exclusive in-tile offsets
-    uint32_t prefix[2];          // exclusive prefix of the tile over all earlier tiles
-    uint32_t ok[2];              // look-back finished in time
-    uint32_t ticket[2];
-    uint32_t tag;
-    uint32_t abort;
+const PipeConfig kPipeConfigs[kNumPipeConfigs] = {
+    {8, 8, 3, 1}, {8, 4, 4, 1}, {8, 16, 2, 1}, {4, 8, 5, 1}, {16, 4, 2, 1}, {8, 8, 3, 0},
 };
 
-// What a tile buffer holds per domain index: the gathered element (gather),
-// the image itself (indices), or the image as a 32-bit target slot (scatter:
-// out[f(i_j)] = in[j] reads its element once the tile's ranks are known).
-template <class T, Mode MODE>
-using PipeSlot = typename std::conditional<MODE == Mode::Scatter, uint32_t, T>::type;
+namespace {
 
-template <class T, Mode MODE, bool ODD, int NCW, int ITEMS>
-__global__ void __launch_bounds__((NCW + 1) * 32, BSHUFFLE_PIPE_MIN_CTAS) pipe_tile_kernel(const __grid_constant__ TileArgs a)
+std::atomic<int> g_pipe_selected[5];  // per width class: 1, 2, 4, 8, 16 bytes
+
+int width_slot(uint32_t elem_bytes)
 {
-    using S = PipeSlot<T, MODE>;
-    constexpr uint32_t NCT = NCW * 32;  // compute threads
-    constexpr uint32_t TILE = NCT * ITEMS;
-    constexpr int E = NCW * ITEMS;
-    __shared__ PipeShared<NCW, ITEMS> sh;
-    extern __shared__ __align__(16) unsigned char pipe_dyn[];
-    S *vals = reinterpret_cast<S *>(pipe_dyn);  // [2][TILE], natural (item, thread) order
-
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t warp = threadIdx.x >> 5;
-    // a wait for the other role gets room for one full look-back timeout
-    const uint64_t role_limit = 2 * a.timeout_ns + 1000000000ull;
-
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < 2; ++b) {
-            dev::mbar_init(&sh.full[b], NCW);
-            dev::mbar_init(&sh.ranked[b], 1);
-            sh.aggc[b] = 0ull;
-        }
-        sh.tag = dev::ld_relaxed_gpu(&a.ws->tag);
-        sh.abort = 0u;
+    switch (elem_bytes) {
+    case 4: return 2;
+    case 8: return 3;
+    case 16: return 4;
+    default: return -1;
     }
-    __syncthreads();
-    const uint32_t tag = sh.tag;
-    const dev::StatusRing ring{a.status, ~0ull, 63u, tag};
-    volatile uint32_t *abort = &sh.abort;
-
-    if (warp < NCW) {
-        // ---------------------------------------------------------- compute
-        const uint32_t ct = threadIdx.x;
-        const uint32_t lt = dev::lanemask_lt();
-        const T *in = static_cast<const T *>(a.in);
-        T *out = static_cast<T *>(a.out);
-        for (uint32_t iter = 0;; ++iter) {
-            const int b = static_cast<int>(iter & 1u);
-            if (ct == 0) sh.ticket[b] = *abort == 0u ? atomicAdd(&a.ws->ticket, 1u) : 0xffffffffu;
-            dev::compute_sync(NCT);
-            const uint32_t tile = sh.ticket[b];
-            const bool stop = tile >= a.num_tiles;
-            if (!stop) {
-                const uint32_t base = tile * TILE;
-                uint32_t left[ITEMS], right[ITEMS];
-#pragma unroll
-                for (int j = 0; j < ITEMS; ++j) {
-                    const uint32_t i = base + static_cast<uint32_t>(j) * NCT + ct;
-                    left[j] = i >> a.g.R;
-                    right[j] = i & a.g.rmask;
-                }
-                dev::cipher_items<ODD, ITEMS>(left, right, a.keys, a.rounds, a.g);
-                S *buf = vals + static_cast<size_t>(b) * TILE;
-                uint32_t count = 0;
-#pragma unroll
-                for (int j = 0; j < ITEMS; ++j) {
-                    const uint32_t i = base + static_cast<uint32_t>(j) * NCT + ct;
-                    const uint32_t src = (left[j] << a.g.R) | right[j];
-                    const bool keep = static_cast<uint64_t>(i) < a.g.domain && src < a.g.n;
-                    if (keep) {
-                        S *slot = buf + static_cast<uint32_t>(j) * NCT + ct;
-                        if constexpr (MODE == Mode::Gather)
-                            dev::cp_async<sizeof(T)>(slot, in + src);
-                        else
-                            *slot = static_cast<S>(src);
-                    }
-                    const uint32_t m = __ballot_sync(kFull, keep);
-                    count += __popc(m);
-                    if (lane == 0) sh.masks[b][j * NCW + warp] = m;
-                }
-                if (lane == 0) {
-                    const unsigned long long v = atomicAdd(&sh.aggc[b], (1ull << 32) | count);
-                    if ((v >> 32) == NCW - 1 && static_cast<int64_t>(tile) != a.skip_publish_tile) {
-                        const uint32_t total = static_cast<uint32_t>(v) + count;
-                        dev::st_relaxed_gpu(ring.slot(tile), dev::status_word(tag, tile == 0u, total));
-                    }
-                }
-            }
-            dev::cp_async_commit();
-            __syncwarp();
-            if (lane == 0) dev::mbar_arrive(&sh.full[b]);
-            if (iter > 0) {
-                // store the previous tile (buffer b ^ 1) once it is ranked
-                const int pb = b ^ 1;
-                const bool ranked = dev::mbar_wait(&sh.ranked[pb], ((iter - 1u) >> 1) & 1u, role_limit, abort);
-                if (!ranked) {
-                    if (lane == 0) dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
-                    *abort = 1u;
-                }
-                dev::cp_async_wait_prior();  // this thread's copies of the previous tile have landed
-                if (ranked && sh.ok[pb] != 0u) {
-                    const S *pbuf = vals + static_cast<size_t>(pb) * TILE;
-                    const uint32_t prefix = sh.prefix[pb];
-                    if constexpr (MODE == Mode::Scatter) {
-                        // coalesced reads of this tile's slots, then the random writes
-                        uint32_t target[ITEMS];
-                        T val[ITEMS];
-#pragma unroll
-                        for (int j = 0; j < ITEMS; ++j) {
-                            const uint32_t e = static_cast<uint32_t>(j) * NCW + warp;
-                            const uint32_t m = sh.masks[pb][e];
-                            target[j] = 0xffffffffu;
-                            if ((m >> lane) & 1u) {
-                                const uint32_t dst = prefix + sh.offs[pb][e] + __popc(m & lt);
-                                if (dst < a.g.n) {
-                                    target[j] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
-                                    val[j] = __ldg(in + dst);
-                                } else {
-                                    dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int j = 0; j < ITEMS; ++j)
-                            if (target[j] < a.g.n) out[target[j]] = val[j];
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < ITEMS; ++j) {
-                            const uint32_t e = static_cast<uint32_t>(j) * NCW + warp;
-                            const uint32_t m = sh.masks[pb][e];
-                            if ((m >> lane) & 1u) {
-                                const uint32_t dst = prefix + sh.offs[pb][e] + __popc(m & lt);
-                                if (dst < a.g.n) out[dst] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
-                                else dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
-                            }
-                        }
-                    }
-                }
-            }
-            if (stop) break;
-        }
-        dev::cp_async_wait_all();
-    } else {
-        // -------------------------------------------------------- look-back
-        for (uint32_t iter = 0;; ++iter) {
-            const int b = static_cast<int>(iter & 1u);
-            const uint32_t parity = (iter >> 1) & 1u;
-            // lane 0 waits, so that the warp leaves the loop as one
-            bool full = false;
-            if (lane == 0) {
-                full = dev::mbar_wait(&sh.full[b], parity, role_limit, abort);
-                if (!full) {
-                    dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
-                    *abort = 1u;
-                }
-            }
-            if (!__shfl_sync(kFull, full, 0)) break;
-            (void)dev::mbar_test(&sh.full[b], parity);  // completed phase: every lane acquires it
-            const uint32_t tile = sh.ticket[b];
-            if (tile >= a.num_tiles) break;
-            constexpr int C = (E + 31) / 32;
-            uint32_t local[C];
-            uint32_t sum = 0;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const int e = static_cast<int>(lane) * C + c;
-                local[c] = e < E ? static_cast<uint32_t>(__popc(sh.masks[b][e])) : 0u;
-                sum += local[c];
-            }
-            const uint32_t incl = dev::warp_inclusive_scan(sum);
-            uint32_t run = incl - sum;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const int e = static_cast<int>(lane) * C + c;
-                if (e < E) sh.offs[b][e] = run;
-                run += local[c];
-            }
-            const uint32_t aggregate = __shfl_sync(kFull, incl, 31);
-            uint32_t prefix = 0;
-            bool ok = true;
-            if (tile > 0u) {
-                prefix = dev::lookback(ring, tile, 0, a.timeout_ns, ok);
-                if (lane == 0 && static_cast<int64_t>(tile) != a.skip_publish_tile)
-                    dev::st_relaxed_gpu(ring.slot(tile), dev::status_word(tag, true, prefix + aggregate));
-                if (lane == 0 && !ok) dev::record_error(a.ws, dev::kErrLookbackTimeout, tile);
-            }
-            if (lane == 0) {
-                sh.prefix[b] = prefix;
-                sh.ok[b] = ok ? 1u : 0u;
-                sh.aggc[b] = 0ull;
-            }
-            __syncwarp();
-            if (lane == 0) dev::mbar_arrive(&sh.ranked[b]);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) dev::finish_launch(a.ws, tag, gridDim.x);
 }
 
 template <class T, Mode MODE>
-cudaError_t launch_typed(const TileArgs &a, cudaStream_t stream)
+cudaError_t launch_default(const TileArgs &a, cudaStream_t stream)
 {
-    constexpr int NCW = kPipeComputeWarps, ITEMS = pipe_items(sizeof(T));
-    constexpr int THREADS = (NCW + 1) * 32;
-    constexpr size_t DYN = sizeof(PipeSlot<T, MODE>) * 2 * pipe_tile(sizeof(T));
-    static std::atomic<int> per_sm[64][2];  // CTAs to launch per device and parity, 0 until first use
-    int device = 0;
-    cudaError_t e = cudaGetDevice(&device);
-    if (e != cudaSuccess) return e;
-    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    const bool odd = (a.g.k & 1u) != 0u;
-    auto kernel = odd ? pipe_tile_kernel<T, MODE, true, NCW, ITEMS> : pipe_tile_kernel<T, MODE, false, NCW, ITEMS>;
-    std::atomic<int> &slot = per_sm[device][odd ? 1 : 0];
-    int ctas = slot.load(std::memory_order_acquire);
-    if (ctas == 0) {
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(DYN));
-        if (e != cudaSuccess) return e;
-        int blocks = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, THREADS, DYN);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-        if (e != cudaSuccess) return e;
-        ctas = (blocks > 0 ? blocks : 1) * sms;
-        slot.store(ctas, std::memory_order_release);
-    }
-    const uint32_t grid = a.num_tiles < static_cast<uint32_t>(ctas) ? a.num_tiles : static_cast<uint32_t>(ctas);
-    kernel<<<grid, THREADS, DYN, stream>>>(a);
-    return cudaGetLastError();
+    return pipe::launch_shape<T, MODE, 8, 8, 3, true>(a, stream);
 }
 
 }  // namespace
 
-uint32_t pipe_tile_size(uint32_t elem_bytes) { return pipe_tile(elem_bytes); }
+int pipe_config_for(uint32_t elem_bytes, Mode mode)
+{
+    const int slot = width_slot(elem_bytes);
+    if (mode != Mode::Gather || slot < 0) return 0;
+    return g_pipe_selected[slot].load();
+}
+
+int select_pipe_config(uint32_t elem_bytes, int config)
+{
+    const int slot = width_slot(elem_bytes);
+    if (slot < 0 || config < 0 || config >= kNumPipeConfigs) return -1;
+    g_pipe_selected[slot].store(config);
+    return 0;
+}
+
+int selected_pipe_config(uint32_t elem_bytes)
+{
+    const int slot = width_slot(elem_bytes);
+    return slot < 0 ? 0 : g_pipe_selected[slot].load();
+}
+
+uint32_t pipe_tile_size(uint32_t, int config)
+{
+    const PipeConfig &c = kPipeConfigs[config >= 0 && config < kNumPipeConfigs ? config : 0];
+    return static_cast<uint32_t>(c.warps * 32 * c.items);
+}
 
 bool pipe_supports(Mode mode, uint32_t elem_bytes)
 {
@@ -308,23 +78,27 @@ bool pipe_supports(Mode mode, uint32_t elem_bytes)
     return false;
 }
 
-cudaError_t launch_pipe(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream)
+cudaError_t launch_pipe(const TileArgs &a, Mode mode, uint32_t elem_bytes, int config, cudaStream_t stream)
 {
+    if (config != 0) {
+        if (mode != Mode::Gather) return cudaErrorInvalidValue;
+        return launch_pipe_tuned(a, elem_bytes, config, stream);
+    }
     switch (mode) {
-    case Mode::Index32: return launch_typed<unsigned int, Mode::Index32>(a, stream);
-    case Mode::Index64: return launch_typed<unsigned long long, Mode::Index64>(a, stream);
+    case Mode::Index32: return launch_default<unsigned int, Mode::Index32>(a, stream);
+    case Mode::Index64: return launch_default<unsigned long long, Mode::Index64>(a, stream);
     case Mode::Gather:
         switch (elem_bytes) {
-        case 4: return launch_typed<unsigned int, Mode::Gather>(a, stream);
-        case 8: return launch_typed<unsigned long long, Mode::Gather>(a, stream);
-        case 16: return launch_typed<uint4, Mode::Gather>(a, stream);
+        case 4: return launch_default<unsigned int, Mode::Gather>(a, stream);
+        case 8: return launch_default<unsigned long long, Mode::Gather>(a, stream);
+        case 16: return launch_default<uint4, Mode::Gather>(a, stream);
         default: return cudaErrorInvalidValue;
         }
     case Mode::Scatter:
         switch (elem_bytes) {
-        case 4: return launch_typed<unsigned int, Mode::Scatter>(a, stream);
-        case 8: return launch_typed<unsigned long long, Mode::Scatter>(a, stream);
-        case 16: return launch_typed<uint4, Mode::Scatter>(a, stream);
+        case 4: return launch_default<unsigned int, Mode::Scatter>(a, stream);
+        case 8: return launch_default<unsigned long long, Mode::Scatter>(a, stream);
+        case 16: return launch_default<uint4, Mode::Scatter>(a, stream);
         default: return cudaErrorInvalidValue;
         }
     }
