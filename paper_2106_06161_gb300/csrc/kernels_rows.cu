@@ -112,6 +112,146 @@ __global__ void __launch_bounds__(kRowBlock) rows_tile_kernel(const __grid_const
     if (threadIdx.x == 0) dev::finish_launch(a.ws, st.tag, gridDim.x);
 }
 
+// ------------------------------------------------------------------ two-kernel form
+//
+// For up to kRowsSumTiles tiles the inter-tile prefix needs no chain: the
+// count kernel writes every tile's kept count (one small CTA per tile, no
+// data read), and each CTA of the copy kernel adds the counts of the tiles
+// before it itself (at most a few thousand L2-resident words).  The copy
+// kernel is a programmatic dependent launch: its CTAs evaluate the bijection
+// and rank their tile while the count kernel runs, and wait for it
+// (griddepcontrol.wait) only before reading the counts.  Counts are stored
+// as tile-status words with tag 0, which no look-back ever accepts.
+constexpr uint32_t kRowsSumTiles = 4096;
+
+__device__ __forceinline__ void wait_for_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_grid() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+template <bool ODD, int ROWS>
+__global__ void __launch_bounds__(ROWS) rows_count_kernel(const __grid_constant__ TileArgs a)
+{
+    allow_dependent_grid();
+    __shared__ uint32_t s_count[ROWS / 32];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t i = blockIdx.x * static_cast<uint32_t>(ROWS) + threadIdx.x;
+    uint32_t left[1] = {i >> a.g.R};
+    uint32_t right[1] = {i & a.g.rmask};
+    dev::cipher_items<ODD, 1>(left, right, a.keys, a.rounds, a.g);
+    const uint32_t src = (left[0] << a.g.R) | right[0];
+    const bool keep = static_cast<uint64_t>(i) < a.g.domain && src < a.g.n;
+    const uint32_t c = __popc(__ballot_sync(kFull, keep));
+    if (lane == 0) s_count[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t total = 0;
+        for (int w = 0; w < ROWS / 32; ++w) total += s_count[w];
+        a.status[blockIdx.x] = total;  // tag 0: never read as a published status
+    }
+}
+
+template <Mode MODE, bool ODD, int ROWS>
+__global__ void __launch_bounds__(kRowBlock) rows_copy_kernel(const __grid_constant__ TileArgs a)
+{
+    constexpr int WARPS = kRowBlock / 32;
+    constexpr int TILE_WARPS = ROWS / 32;
+    __shared__ uint32_t s_counts[TILE_WARPS];
+    __shared__ uint32_t s_src[ROWS];
+    __shared__ uint32_t s_dst[ROWS];
+    __shared__ uint32_t s_prefix, s_total;
+
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t tile = blockIdx.x;
+    const bool owner = warp < static_cast<uint32_t>(TILE_WARPS);
+    const uint32_t i = tile * static_cast<uint32_t>(ROWS) + threadIdx.x;
+    bool keep = false;
+    uint32_t src = 0, mask = 0;
+    if (owner) {
+        uint32_t left[1] = {i >> a.g.R};
+        uint32_t right[1] = {i & a.g.rmask};
+        dev::cipher_items<ODD, 1>(left, right, a.keys, a.rounds, a.g);
+        src = (left[0] << a.g.R) | right[0];
+        keep = static_cast<uint64_t>(i) < a.g.domain && src < a.g.n;
+        mask = __ballot_sync(kFull, keep);
+        if (lane == 0) s_counts[warp] = __popc(mask);
+    }
+    // the counts of the tiles before this one
+    wait_for_prerequisite_grid();
+    if (warp == 0) {
+        uint32_t sum = 0;
+        for (uint32_t t = lane; t < tile; t += 32u) sum += static_cast<uint32_t>(a.status[t]);
+        sum = __reduce_add_sync(kFull, sum);
+        if (lane == 0) s_prefix = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < TILE_WARPS; ++w) {
+            const uint32_t c = s_counts[w];
+            s_counts[w] = run;
+            run += c;
+        }
+        s_total = run;
+    }
+    __syncthreads();
+    const uint32_t prefix = s_prefix;
+    if (keep) {
+        const uint32_t local = s_counts[warp] + __popc(mask & dev::lanemask_lt());
+        const uint32_t dst = prefix + local;
+        if (dst >= a.g.n) {
+            dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
+            keep = false;
+        }
+        s_src[local] = keep ? src : 0xffffffffu;
+        s_dst[local] = dst;
+    }
+    __syncthreads();
+    const uint32_t count = s_total;
+    const uint32_t chunks = a.elem_bytes / 16u;
+    const uint4 *in = static_cast<const uint4 *>(a.in);
+    uint4 *out = static_cast<uint4 *>(a.out);
+    for (uint32_t r = warp; r < count; r += WARPS) {
+        const uint32_t s = s_src[r];
+        if (s == 0xffffffffu) continue;
+        const uint64_t from_row = MODE == Mode::Gather ? s : s_dst[r];
+        const uint64_t to_row = MODE == Mode::Gather ? s_dst[r] : s;
+        const uint4 *from = in + from_row * chunks;
+        uint4 *to = out + to_row * chunks;
+        for (uint32_t c0 = 0; c0 < chunks; c0 += 32u * kRowChunkUnroll) {
+            uint4 v[kRowChunkUnroll];
+#pragma unroll
+            for (int u = 0; u < kRowChunkUnroll; ++u) {
+                const uint32_t c = c0 + static_cast<uint32_t>(u) * 32u + lane;
+                if (c < chunks) v[u] = __ldg(from + c);
+            }
+#pragma unroll
+            for (int u = 0; u < kRowChunkUnroll; ++u) {
+                const uint32_t c = c0 + static_cast<uint32_t>(u) * 32u + lane;
+                if (c < chunks) to[c] = v[u];
+            }
+        }
+    }
+}
+
+template <Mode MODE, bool ODD, int ROWS>
+cudaError_t launch_two_kernel(const TileArgs &a, cudaStream_t stream)
+{
+    rows_count_kernel<ODD, ROWS><<<a.num_tiles, ROWS, 0, stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.num_tiles, 1, 1);
+    cfg.blockDim = dim3(kRowBlock, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, rows_copy_kernel<MODE, ODD, ROWS>, a);
+}
+
 }  // namespace
 
 uint32_t rows_tile_size(uint32_t row_bytes) { return rows_per_tile(row_bytes); }
@@ -135,9 +275,16 @@ cudaError_t launch_rows_t(const TileArgs &a, Mode mode, cudaStream_t stream)
         ctas_cached = (blocks > 0 ? blocks : 1) * sms;
         per_sm[device].store(ctas_cached, std::memory_order_release);
     }
+    const bool odd = (a.g.k & 1u) != 0u;
+    if (a.num_tiles <= kRowsSumTiles && (mode == Mode::Gather || mode == Mode::Scatter)) {
+        if (mode == Mode::Gather)
+            return odd ? launch_two_kernel<Mode::Gather, true, ROWS>(a, stream)
+                       : launch_two_kernel<Mode::Gather, false, ROWS>(a, stream);
+        return odd ? launch_two_kernel<Mode::Scatter, true, ROWS>(a, stream)
+                   : launch_two_kernel<Mode::Scatter, false, ROWS>(a, stream);
+    }
     const uint32_t ctas = a.num_tiles < static_cast<uint32_t>(ctas_cached) ? a.num_tiles : ctas_cached;
     const dim3 grid(ctas), block(kRowBlock);
-    const bool odd = (a.g.k & 1u) != 0u;
     if (mode == Mode::Gather) {
         if (odd) rows_tile_kernel<Mode::Gather, true, ROWS><<<grid, block, 0, stream>>>(a);
         else rows_tile_kernel<Mode::Gather, false, ROWS><<<grid, block, 0, stream>>>(a);

@@ -216,3 +216,14 @@ def test_fusion_ablation_variants_match_oracle(variant):
             bs.bshuffle_permute_ablation(xd.data_ptr(), out.data_ptr(), n, width, 13, 24, variant, stream)
             assert_no_device_error()
             assert np.array_equal(to_host(out, x), oracle.permute(x, 13)), (width, n)
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_rows_both_forms(width):
+    # rows of 32 and 64 bytes: up to 4,096 tiles the two-kernel form (a count
+    # kernel, then a copy kernel that sums the counts before its tile),
+    # beyond it the persistent kernel with the decoupled look-back
+    for n in (5_000, 300_001, 2**20 + 3):
+        x = _payload(n, width, 1)
+        assert np.array_equal(gpu_permute(x, 21), oracle.permute_mt(x, 21)), n
+        assert np.array_equal(gpu_inverse(x, 21), oracle.inverse(x, 21)), n
