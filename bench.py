@@ -75,6 +75,10 @@ def parse():
                    help="only run warmup + steps launches of the uint64 shuffle at this n (for ncu)")
     p.add_argument("--table1", action="store_true",
                    help="only print the Table 1 layout: M items/s of 64-bit keys at lengths 2^w + 1")
+    p.add_argument("--lookback-share", action="store_true",
+                   help="only measure the share of CTA time the single passes wait on the look-back "
+                        "(builds the library with BSHUFFLE_LOOKBACK_CLOCKS=1 into its own directory)")
+    p.add_argument("--no-tune", action="store_true", help="skip the autotuner (for launch lists)")
     return p.parse_args()
 
 
@@ -350,7 +354,7 @@ def run_ours(args):
     # pipelined single passes and of the batched kernel (4 and 8 bytes: the
     # widths the bench runs them at); a few seconds
     from paper_2106_06161_gb300 import autotune
-    tuning = autotune.tune(widths=(4, ELEM), reps=3, warmup=1, save=False)
+    tuning = None if args.no_tune else autotune.tune(widths=(4, ELEM), reps=3, warmup=1, save=False)
 
     seed = SEED + rank
     host = workloads.uniform_u64(N_MAIN, seed)
@@ -860,9 +864,58 @@ def table1(args):
                       "gpu": torch.cuda.get_device_name(), "rows": rows}), flush=True)
 
 
+def lookback_share(args):
+    """Share of CTA time the plain and the pipelined single pass wait on the
+    inter-tile look-back, from SM clock cycles counted on the device by a
+    measurement build of the library (BSHUFFLE_LOOKBACK_CLOCKS=1), at the
+    worst-case padding n = 2^28 + 12345 and at n = 2^28 (uint64)."""
+    import ctypes
+
+    import torch
+    from paper_2106_06161_gb300 import build as bsbuild
+    path = bsbuild.build(defines=("BSHUFFLE_LOOKBACK_CLOCKS=1",),
+                         build_dir=os.path.join(bsbuild.HERE, "_build_clocks"))
+    lib = ctypes.CDLL(path)
+    lib.bshuffle_permute.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]
+    lib.bshuffle_debug_lookback_cycles.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64),
+                                                   ctypes.POINTER(ctypes.c_uint64)]
+    lib.bshuffle_get_error.argtypes = [ctypes.c_void_p]
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    rows = {}
+    for n in (N_WORST, N_MAIN):
+        x = torch.from_numpy(workloads.uniform_u64(n, 1).view(np.int64)).cuda()
+        y = torch.empty_like(x)
+        for name, strat in (("single_pass", 1), ("pipelined", 3)):
+            lib.bshuffle_set_strategy(strat)
+            f = lambda: lib.bshuffle_permute(x.data_ptr(), y.data_ptr(), n, ELEM, 1, ROUNDS, sptr)  # noqa: E731
+            for _ in range(max(3, args.warmup)):
+                f()
+            lb, cta = ctypes.c_uint64(0), ctypes.c_uint64(0)
+            rc = lib.bshuffle_debug_lookback_cycles(sptr, ctypes.byref(lb), ctypes.byref(cta))
+            if rc != 0:
+                raise SystemExit(f"measurement build not active ({rc})")
+            _, region = timed_launches(f, args.steps, stream, torch)
+            rc = lib.bshuffle_debug_lookback_cycles(sptr, ctypes.byref(lb), ctypes.byref(cta))
+            if rc != 0 or lib.bshuffle_get_error(sptr) != 0:
+                raise SystemExit("device error")
+            rows[f"n={n} {name}"] = {"lookback_share": lb.value / cta.value if cta.value else None,
+                                     "lookback_cycles": lb.value, "cta_cycles": cta.value,
+                                     "ms_per_launch_measurement_build": region / args.steps}
+        lib.bshuffle_set_strategy(0)
+        del x, y
+    print(json.dumps({"lookback_share": rows, "launches": args.steps,
+                      "definition": "plain kernel: cycles of each tile's look-back (its other warps wait at the "
+                                    "barrier) / cycles of its CTAs; pipelined kernel: cycles its compute warps "
+                                    "wait for a tile's rank / cycles of its persistent CTAs"}), flush=True)
+
+
 def main():
     args = parse()
-    if args.table1:
+    if args.lookback_share:
+        lookback_share(args)
+    elif args.table1:
         table1(args)
     elif args.profile_batched:
         profile_batched(args)

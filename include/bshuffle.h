@@ -453,6 +453,19 @@ int bshuffle_set_lookback_timeout_ns(uint64_t ns);
 int bshuffle_debug_skip_publish(int64_t tile);
 
 /*
+ * Measurement aid.  A library built with BSHUFFLE_LOOKBACK_CLOCKS=1 (an nvcc
+ * define; the default build has it off and pays nothing) adds, per stream,
+ * the SM clock cycles its single-pass kernels wait on the inter-tile
+ * look-back (the plain kernel: cycles of the look-back itself, while the
+ * tile's other warps wait at the barrier; the pipelined kernel: cycles the
+ * compute warps wait for a tile's rank) and the cycles their CTAs run.  This
+ * call synchronises `stream`, writes both sums and clears them; their ratio
+ * is the share of CTA time lost to the look-back chain of Sec. 4's single
+ * pass.  Returns BSHUFFLE_ERR_INVALID (and zeros) in the default build.
+ */
+int bshuffle_debug_lookback_cycles(void *stream, uint64_t *lookback_cycles, uint64_t *cta_cycles);
+
+/*
  * Allocation-free variant of bshuffle_permute, for callers that cannot
  * allocate device memory when they call: a process that has reserved all of
  * the device's memory for its own pool (cudaMalloc would fail), or a

@@ -53,6 +53,7 @@ SIGNATURES = {
     "bshuffle_release_workspaces": (_int, []),
     "bshuffle_set_lookback_timeout_ns": (_int, [_u64]),
     "bshuffle_debug_skip_publish": (_int, [_i64]),
+    "bshuffle_debug_lookback_cycles": (_int, [_p, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "bshuffle_version": (_int, []),
     "bshuffle_permute_static": (_int, [_p, _p, _u64, _u32, _u64, _u32, _p]),
     "bshuffle_mc_group_diff": (_int, [_p, _u64, _u64, _u64, _u32, _u32, _p, _p]),

@@ -66,21 +66,27 @@ def kernel_fingerprint(source: str) -> str:
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link the library; returns the path of the shared object."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, defines: tuple = (), build_dir: str | None = None) -> str:
+    """Compile and link the library; returns the path of the shared object.
+
+    `defines` (e.g. ("BSHUFFLE_LOOKBACK_CLOCKS=1",)) builds a variant of the
+    library; give it its own `build_dir` so that the default build stays."""
+    bdir = BUILD_DIR if build_dir is None else build_dir
+    lib_path = os.path.join(bdir, LIB_NAME)
+    extra = [f"-D{d}" for d in defines]
+    os.makedirs(bdir, exist_ok=True)
     sources = _sources()
-    stamp_path = os.path.join(BUILD_DIR, "stamp.txt")
-    fp = _fingerprint(sources)
-    if not force and os.path.exists(LIB_PATH) and os.path.exists(stamp_path):
+    stamp_path = os.path.join(bdir, "stamp.txt")
+    fp = _fingerprint(sources) + ("|" + ",".join(defines) if defines else "")
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp_path):
         with open(stamp_path) as fh:
             if fh.read().strip() == fp:
-                return LIB_PATH
+                return lib_path
     nvcc = _nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         res = subprocess.run(cmd, capture_output=True, text=True)
@@ -92,14 +98,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(sources))) as ex:
         objs = list(ex.map(compile_one, sources))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     res = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"linking {LIB_NAME} failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB_PATH)
+    os.replace(tmp, lib_path)
     with open(stamp_path, "w") as fh:
         fh.write(fp)
-    return LIB_PATH
+    return lib_path
 
 
 if __name__ == "__main__":

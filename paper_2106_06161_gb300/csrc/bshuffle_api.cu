@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/bshuffle.h"
+#include "bshuffle_device.cuh"
 #include "bshuffle_internal.h"
 
 namespace {
@@ -1002,6 +1003,32 @@ int bshuffle_set_lookback_timeout_ns(uint64_t ns)
 {
     g_timeout_ns.store(ns < 1000000ull ? 1000000ull : ns);
     return BSHUFFLE_OK;
+}
+
+int bshuffle_debug_lookback_cycles(void *stream_ptr, uint64_t *lookback_cycles, uint64_t *cta_cycles)
+{
+    if (lookback_cycles == nullptr || cta_cycles == nullptr) return BSHUFFLE_ERR_NULL;
+    *lookback_cycles = 0;
+    *cta_cycles = 0;
+    if (BSHUFFLE_LOOKBACK_CLOCKS == 0) return BSHUFFLE_ERR_INVALID;  // not a measurement build
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lock(g_mutex);
+    auto it = g_workspaces.find({device, reinterpret_cast<uintptr_t>(stream)});
+    if (it == g_workspaces.end() || it->second.base == nullptr) return BSHUFFLE_OK;
+    WsHeader h{};
+    e = cudaMemcpy(&h, it->second.base, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *lookback_cycles = h.lookback_cycles;
+    *cta_cycles = h.cta_cycles;
+    const size_t off = offsetof(WsHeader, lookback_cycles);
+    e = cudaMemsetAsync(static_cast<char *>(it->second.base) + off, 0, 2 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 
 int bshuffle_debug_skip_publish(int64_t tile)

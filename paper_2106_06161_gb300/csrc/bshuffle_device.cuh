@@ -205,6 +205,27 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
+// Look-back clocks (a measurement build, off by default): with
+// BSHUFFLE_LOOKBACK_CLOCKS=1 the single-pass kernels add the SM clock cycles
+// their tiles wait on the look-back, and the cycles their CTAs run, to the
+// workspace header, so that the share of time lost to the inter-tile chain
+// is measured directly.  Otherwise these helpers compile to nothing.
+#ifndef BSHUFFLE_LOOKBACK_CLOCKS
+#define BSHUFFLE_LOOKBACK_CLOCKS 0
+#endif
+constexpr bool kLookbackClocks = BSHUFFLE_LOOKBACK_CLOCKS != 0;
+
+__device__ __forceinline__ long long clock_mark()
+{
+    if constexpr (kLookbackClocks) return clock64();
+    return 0;
+}
+
+__device__ __forceinline__ void clock_add(unsigned long long *acc, long long since)
+{
+    if constexpr (kLookbackClocks) atomicAdd(acc, static_cast<unsigned long long>(clock64() - since));
+}
+
 __device__ __forceinline__ void record_error(WsHeader *ws, int code, uint64_t info)
 {
     if (atomicCAS(&ws->error, 0, code) == 0)
@@ -378,7 +399,9 @@ __device__ __forceinline__ void tile_scan_lookback(TileShared<ENTRIES> &st, cons
     uint32_t exclusive = 0;
     bool ok = true;
     if (tile > first) {
+        const long long c0 = clock_mark();
         exclusive = lookback(ring, tile, first, timeout_ns, ok);
+        if (lane == 0) clock_add(&ws->lookback_cycles, c0);
         if (lane == 0 && publish) st_relaxed_gpu(ring.slot(tile), status_word(tag, true, exclusive + aggregate));
         if (lane == 0 && !ok) record_error(ws, kErrLookbackTimeout, tile);
     }

@@ -21,6 +21,11 @@ struct WsHeader {
     uint64_t error_info;  // detail of that error (tile index or slot)
     uint32_t batch_ticket;  // ticket of the persistent batched kernel
     uint32_t batch_done;    // finished CTAs of the persistent batched kernel
+    // Built with BSHUFFLE_LOOKBACK_CLOCKS=1 only: SM clock cycles that tiles
+    // waited on the look-back, and cycles the CTAs ran (plain and pipelined
+    // single passes); 0 otherwise.
+    unsigned long long lookback_cycles;
+    unsigned long long cta_cycles;
 };
 
 // Shape of one shuffle: n kept slots out of a 2^k domain whose indices are

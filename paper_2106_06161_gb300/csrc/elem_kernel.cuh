@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant_
     constexpr int WARPS = BLOCK / 32;
     constexpr int ENTRIES = ITEMS * WARPS;
     __shared__ dev::TileShared<ENTRIES> st;
+    const long long c0 = dev::clock_mark();
 
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
@@ -165,7 +166,10 @@ __global__ void __launch_bounds__(BLOCK) elem_tile_kernel(const __grid_constant_
                 if (keep[j]) out[src[j]] = val[j];
         }
     }
-    if (threadIdx.x == 0) dev::finish_launch(a.ws, tag, gridDim.x);
+    if (threadIdx.x == 0) {
+        dev::clock_add(&a.ws->cta_cycles, c0);
+        dev::finish_launch(a.ws, tag, gridDim.x);
+    }
 }
 
 // Launch one configuration; the caller has checked rounds against ROUNDS.

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const _
     constexpr uint32_t TILE = NCT * ITEMS;
     constexpr int E = NCW * ITEMS;
     __shared__ PipeShared<NCW, ITEMS> sh;
+    const long long c_start = dev::clock_mark();
     extern __shared__ __align__(16) unsigned char pipe_dyn[];
     S *vals = reinterpret_cast<S *>(pipe_dyn);  // [2][TILE], natural (item, thread) order
 
@@ -153,7 +154,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const _
             if (iter > 0) {
                 // store the previous tile (buffer b ^ 1) once it is ranked
                 const int pb = b ^ 1;
+                const long long w0 = dev::clock_mark();
                 const bool ranked = dev::mbar_wait(&sh.ranked[pb], ((iter - 1u) >> 1) & 1u, role_limit, abort);
+                if (ct == 0) dev::clock_add(&a.ws->lookback_cycles, w0);  // the compute warps wait on the rank
                 if (!ranked) {
                     if (lane == 0) dev::record_error(a.ws, dev::kErrLookbackTimeout, iter);
                     *abort = 1u;
@@ -255,7 +258,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const _
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) dev::finish_launch(a.ws, tag, gridDim.x);
+    if (threadIdx.x == 0) {
+        dev::clock_add(&a.ws->cta_cycles, c_start);
+        dev::finish_launch(a.ws, tag, gridDim.x);
+    }
 }
 
 // Launch one shape: persistent CTAs, as many as fit on the device (cached
