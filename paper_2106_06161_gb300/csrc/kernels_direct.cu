@@ -97,6 +97,39 @@ __global__ void __launch_bounds__(kDBlock) direct_rows_kernel(const __grid_const
     const uint32_t chunks = a.elem_bytes / 16u;
     const uint4 *in = static_cast<const uint4 *>(a.in);
     uint4 *out = static_cast<uint4 *>(a.out);
+    if (chunks <= 16u * kRowChunkUnroll) {
+        // rows of up to 2 KiB: two rows loaded before they are stored, so
+        // that each lane keeps up to 8 16-byte loads in flight
+        constexpr int H = kRowChunkUnroll / 2;
+        for (uint32_t r = 0; r < kRowsPerWarp; r += 2) {
+            uint4 v[2][H];
+            uint64_t to_row[2];
+            bool live[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t fr = __shfl_sync(kFull, f[0], r + h);
+                live[h] = fr < n;
+                const uint64_t from_row = MODE == Mode::Gather ? fr : row0 + r + h;
+                to_row[h] = MODE == Mode::Gather ? row0 + r + h : fr;
+                const uint4 *src = in + from_row * chunks;
+#pragma unroll
+                for (int u = 0; u < H; ++u) {
+                    const uint32_t c = static_cast<uint32_t>(u) * 32u + lane;
+                    if (live[h] && c < chunks) v[h][u] = __ldg(src + c);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint4 *dst = out + to_row[h] * chunks;
+#pragma unroll
+                for (int u = 0; u < H; ++u) {
+                    const uint32_t c = static_cast<uint32_t>(u) * 32u + lane;
+                    if (live[h] && c < chunks) dst[c] = v[h][u];
+                }
+            }
+        }
+        return;
+    }
     for (uint32_t r = 0; r < kRowsPerWarp; ++r) {
         const uint32_t fr = __shfl_sync(kFull, f[0], r);
         if (fr >= n) continue;

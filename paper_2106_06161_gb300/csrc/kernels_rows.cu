@@ -210,6 +210,40 @@ __global__ void __launch_bounds__(kRowBlock) rows_copy_kernel(const __grid_const
     const uint32_t chunks = a.elem_bytes / 16u;
     const uint4 *in = static_cast<const uint4 *>(a.in);
     uint4 *out = static_cast<uint4 *>(a.out);
+    if (chunks <= 16u * kRowChunkUnroll) {
+        // rows of up to 2 KiB: a warp loads two rows before storing them, so
+        // that each lane keeps up to 8 16-byte loads in flight
+        constexpr int H = kRowChunkUnroll / 2;
+        for (uint32_t r0 = warp; r0 < count; r0 += 2u * WARPS) {
+            uint4 v[2][H];
+            uint64_t to_row[2];
+            bool live[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t r = r0 + static_cast<uint32_t>(h) * WARPS;
+                const uint32_t s = r < count ? s_src[r] : 0xffffffffu;
+                live[h] = s != 0xffffffffu;
+                const uint64_t from_row = MODE == Mode::Gather ? s : s_dst[r < count ? r : 0];
+                to_row[h] = MODE == Mode::Gather ? s_dst[r < count ? r : 0] : s;
+                const uint4 *from = in + from_row * chunks;
+#pragma unroll
+                for (int u = 0; u < H; ++u) {
+                    const uint32_t c = static_cast<uint32_t>(u) * 32u + lane;
+                    if (live[h] && c < chunks) v[h][u] = __ldg(from + c);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint4 *to = out + to_row[h] * chunks;
+#pragma unroll
+                for (int u = 0; u < H; ++u) {
+                    const uint32_t c = static_cast<uint32_t>(u) * 32u + lane;
+                    if (live[h] && c < chunks) to[c] = v[h][u];
+                }
+            }
+        }
+        return;
+    }
     for (uint32_t r = warp; r < count; r += WARPS) {
         const uint32_t s = s_src[r];
         if (s == 0xffffffffu) continue;
