@@ -70,6 +70,7 @@ def _load():
             "oracle_default_threads": (u32, []),
             "oracle_indices_mt": (u64, [p, u64, u64, u32, u32]),
             "oracle_permute_mt": (u64, [p, p, u64, u32, u64, u32, u32]),
+            "oracle_permute_range_mt": (u64, [p, p, u64, u32, u64, u32, u64, u64, u32]),
             "oracle_sample_permutations": (None, [p, u32, u64, u64, u32]),
             "oracle_fisher_yates": (None, [p, u64, u32, u64]),
             "oracle_mc_statistics": (None, [p, u64, u64, u64, u64, u32, p]),
@@ -225,6 +226,20 @@ def permute_mt(x: np.ndarray, seed: int, rounds: int = DEFAULT_ROUNDS, threads: 
     if got != n:
         raise ValueError(f"threaded permute kept {got} of {n}")
     return out
+
+
+def permute_range_mt(x: np.ndarray, seed: int, first: int, end: int, rounds: int = DEFAULT_ROUNDS,
+                     threads: int = 0) -> np.ndarray:
+    """The kept elements of domain indices [first, end), in order: the output
+    slots of that range of the shuffle, computed on host threads."""
+    x = np.ascontiguousarray(x)
+    n = x.shape[0]
+    out = np.empty((max(min(n, max(end - first, 0)), 1),) + x.shape[1:], dtype=x.dtype)
+    if n == 0 or end <= first:
+        return out[:0]
+    got = _load().oracle_permute_range_mt(_ptr(x), _ptr(out), n, x.nbytes // n, seed & (2**64 - 1), rounds,
+                                          first, end, threads)
+    return out[:got]
 
 
 def sample_permutations(n: int, count: int, seed0: int = 0, rounds: int = DEFAULT_ROUNDS) -> np.ndarray:

@@ -466,6 +466,55 @@ static uint64_t oracle_algorithm1_mt(uint64_t *idx, const void *in, void *out, u
     return total;
 }
 
+/* The kept elements of the domain range [first, end) in increasing domain
+ * order (the output slots of that range, from the range's first slot), on
+ * `threads` host threads over sub-ranges: a bounded sample of a large
+ * shuffle for CPU timing.  Returns the number written. */
+uint64_t oracle_permute_range_mt(const void *in, void *out, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                                 uint32_t rounds, uint64_t first, uint64_t end, uint32_t threads)
+{
+    oracle_range_job jobs[256];
+    uint32_t keys[256];
+    uint32_t k = oracle_domain_bits(n);
+    uint64_t total = 0, span;
+    uint32_t t;
+    if (in == NULL || out == NULL || elem_bytes == 0 || n == 0 || rounds > 256 || k > 40)
+        return 0;
+    if (end > ((uint64_t)1 << k))
+        end = (uint64_t)1 << k;
+    if (first >= end)
+        return 0;
+    if (threads == 0)
+        threads = oracle_default_threads();
+    if (threads > 256)
+        threads = 256;
+    span = end - first;
+    if (threads > span)
+        threads = (uint32_t)span;
+    oracle_round_keys(seed, rounds, keys);
+    for (t = 0; t < threads; t++) {
+        memset(&jobs[t], 0, sizeof(jobs[t]));
+        jobs[t].lo = first + span / threads * t;
+        jobs[t].hi = t + 1 == threads ? end : first + span / threads * (t + 1);
+        jobs[t].n = n;
+        jobs[t].k = k;
+        jobs[t].rounds = rounds;
+        jobs[t].keys = keys;
+        jobs[t].in = (const unsigned char *)in;
+        jobs[t].out = (unsigned char *)out;
+        jobs[t].elem_bytes = elem_bytes;
+    }
+    if (oracle_run_jobs(oracle_range_count, jobs, threads) != 0)
+        return 0;
+    for (t = 0; t < threads; t++) {
+        jobs[t].offset = total;
+        total += jobs[t].count;
+    }
+    if (oracle_run_jobs(oracle_range_write, jobs, threads) != 0)
+        return 0;
+    return total;
+}
+
 uint64_t oracle_indices_mt(uint64_t *idx, uint64_t n, uint64_t seed, uint32_t rounds, uint32_t threads)
 {
     return oracle_algorithm1_mt(idx, NULL, NULL, n, 0, oracle_domain_bits(n), seed, rounds, threads);

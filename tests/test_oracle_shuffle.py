@@ -155,3 +155,18 @@ def test_count_range_gives_the_scan_at_range_boundaries():
     assert start == n
     assert oracle.count_range(n, seed, 0, 2**40) == n  # clipped to the domain
     assert oracle.count_range(n, seed, 5, 5) == 0
+
+
+def test_threaded_range_gives_the_range_slots():
+    # the kept elements of a domain range are the output slots that follow the
+    # earlier ranges' counts
+    n, seed = 50_001, 3
+    x = workloads.uniform_u64(n, 8)
+    full = oracle.permute(x, seed)
+    start = 0
+    for f, e in ((0, 1), (1, 4096), (4096, 40_000), (40_000, 2**16), (2**16, 2**40)):
+        part = oracle.permute_range_mt(x, seed, f, e, threads=3)
+        assert part.shape[0] == oracle.count_range(n, seed, f, e)
+        assert np.array_equal(part, full[start:start + part.shape[0]]), (f, e)
+        start += part.shape[0]
+    assert start == n
