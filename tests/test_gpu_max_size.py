@@ -1,6 +1,6 @@
 """Maximum sizes: n = 2^32 - 1, the library's largest length (domain 2^32,
-k = 32, 16-bit halves), and n = 2^31, the largest length the staged path
-takes.  At n = 2^32 - 1 exactly one domain index is dropped, d = f^-1(n),
+k = 32, 16-bit halves), and n = 2^31, the largest power-of-two length the
+staged path takes.  At n = 2^32 - 1 exactly one domain index is dropped, d = f^-1(n),
 so slot j holds X[f(j)] for j < d and X[f(j + 1)] for j >= d: sampled slots
 are checked against the oracle's bijection and inverse, and sums and extrema
 check that the output is a permutation of the input."""
@@ -40,8 +40,10 @@ def _sample_slots(seed: int) -> np.ndarray:
 
 
 def test_max_length_uint32_iota(bs):
-    # 4-byte elements go through the pipelined kernel; x[i] = i, so the
-    # output is the index sequence itself (16 GiB in, 16 GiB out)
+    # 4-byte elements go through the staged path's ranked form (512 spans of
+    # 2^23 domain indices, each ranked by a cluster of 8 CTAs; 32 GiB of
+    # staging); x[i] = i, so the output is the index sequence itself
+    # (16 GiB in, 16 GiB out)
     seed = 17
     x = torch.arange(N_MAX, dtype=torch.int64, device="cuda").to(torch.int32)
     y = bs.permute(x, seed)
