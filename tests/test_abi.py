@@ -178,3 +178,45 @@ def test_allocation_free_entry_point_argument_errors(lib):
     assert f(a, a + 16, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_ALIAS
     assert f(a + 4, a + 256, 4, 8, 0, 24, None) == L.BSHUFFLE_ERR_ALIGN
     assert f(a, a + 256, 0, 8, 0, 24, None) == L.BSHUFFLE_OK
+
+
+def test_kernel_shape_tables_on_the_host(lib):
+    # describe / select / selected need no device
+    from paper_2106_06161_gb300 import _lib as L
+    for kernel in (L.BSHUFFLE_KERNEL_SINGLE_PASS, L.BSHUFFLE_KERNEL_PIPELINED, L.BSHUFFLE_KERNEL_BATCHED):
+        configs = L.bshuffle_kernel_configs(kernel)
+        assert len(configs) >= 2 and configs[0]["config"] == 0
+        for c in configs:
+            assert c["threads"] % 32 == 0 and c["items"] in (4, 8, 16) and c["rounds_unrolled"] in (0, 24)
+        for w in (4, 8, 16):
+            L.bshuffle_kernel_select(kernel, w, len(configs) - 1)
+            assert L.bshuffle_kernel_selected(kernel, w) == len(configs) - 1
+            L.bshuffle_kernel_select(kernel, w, 0)
+            assert L.bshuffle_kernel_selected(kernel, w) == 0
+    # the single-pass table is the one of bshuffle_tuning_*
+    assert len(L.bshuffle_kernel_configs(L.BSHUFFLE_KERNEL_SINGLE_PASS)) == len(L.bshuffle_tuning_configs())
+    assert lib.bshuffle_kernel_configs(9) == L.BSHUFFLE_ERR_INVALID
+    assert lib.bshuffle_kernel_select(L.BSHUFFLE_KERNEL_PIPELINED, 2, 0) == L.BSHUFFLE_ERR_INVALID
+    assert lib.bshuffle_kernel_select(L.BSHUFFLE_KERNEL_BATCHED, 8, 99) == L.BSHUFFLE_ERR_INVALID
+
+
+def test_lookback_cycles_need_a_measurement_build(lib):
+    # the default build has no cycle accounting: the reader says so
+    from paper_2106_06161_gb300 import _lib as L
+    a, b = ctypes.c_uint64(7), ctypes.c_uint64(7)
+    assert lib.bshuffle_debug_lookback_cycles(None, ctypes.byref(a), ctypes.byref(b)) == L.BSHUFFLE_ERR_INVALID
+    assert a.value == 0 and b.value == 0
+    assert lib.bshuffle_debug_lookback_cycles(None, None, ctypes.byref(b)) == L.BSHUFFLE_ERR_NULL
+
+
+def test_range_entry_points_check_arguments_first(lib):
+    from paper_2106_06161_gb300 import _lib as L
+    buf = (ctypes.c_uint64 * 64)()
+    a = ctypes.addressof(buf)
+    assert lib.bshuffle_count_range(100, 0, 24, 5, 4, a, None) == L.BSHUFFLE_ERR_INVALID
+    assert lib.bshuffle_count_range(100, 0, 99, 0, 4, a, None) == L.BSHUFFLE_ERR_ROUNDS
+    assert lib.bshuffle_count_range(100, 0, 24, 0, 4, a + 4, None) == L.BSHUFFLE_ERR_ALIGN
+    assert lib.bshuffle_permute_range(a, a + 256, 16, 3, 0, 24, 0, 16, 16, None) == L.BSHUFFLE_ERR_ELEM
+    assert lib.bshuffle_permute_range(a, a + 256, 16, 8, 0, 24, 9, 2, 16, None) == L.BSHUFFLE_ERR_INVALID
+    assert lib.bshuffle_permute_range(a, a + 8, 16, 8, 0, 24, 0, 16, 16, None) == L.BSHUFFLE_ERR_ALIAS
+    assert lib.bshuffle_permute_range(a, a + 256, 16, 8, 0, 24, 0, 16, 0, None) == L.BSHUFFLE_OK  # nothing to write
