@@ -79,6 +79,9 @@ def parse():
                    help="only measure the share of CTA time the single passes wait on the look-back "
                         "(builds the library with BSHUFFLE_LOOKBACK_CLOCKS=1 into its own directory)")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner (for launch lists)")
+    p.add_argument("--split", action="store_true",
+                   help="time ONE n=2^28 uint64 shuffle split by domain range across the ranks (strong scaling: "
+                        "each rank counts its range, the counts are all-gathered, each rank gathers its slots)")
     return p.parse_args()
 
 
@@ -917,9 +920,62 @@ def lookback_share(args):
                                     "wait for a tile's rank / cycles of its persistent CTAs"}), flush=True)
 
 
+def run_split(args):
+    """One shuffle split across the ranks by domain range (strong scaling).
+    Every rank holds the whole input; per step it counts its range's kept
+    indices, all-gathers the counts (the one exchange) and gathers its
+    range's kept elements into its run of output slots; the timed region is
+    the slowest rank's.  Exactness is checked against the library's own
+    unsplit shuffle on rank 0's slots."""
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    from paper_2106_06161_gb300 import build as bsbuild
+    if rank == 0 or world == 1:
+        bsbuild.build()
+    barrier(world)
+    import paper_2106_06161_gb300 as bs
+    from paper_2106_06161_gb300 import split
+    bs.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    x = torch.from_numpy(workloads.uniform_u64(N_MAIN, SEED).view(np.int64)).to(dev)
+    exchange = world > 1
+    step = lambda: split.permute_shard(x, SEED, rank, world, ROUNDS, exchange=exchange)  # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        part, offset = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if bs.get_error() != 0:
+        raise SystemExit("device error")
+    region_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    whole = bs.permute(x, SEED, ROUNDS)
+    ok = bool(torch.equal(whole[offset:offset + part.shape[0]], part))
+    if rank == 0:
+        ms = region_ms / args.steps
+        line = {"metric": METRIC, "value": N_MAIN * args.steps / (region_ms * 1e-3), "unit": "elements/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic",
+                "config": dict(workload_config(world), parallelism=f"one shuffle split by domain range over "
+                                                                  f"{world} GPU(s), one all-gather of counts"),
+                "split_equals_unsplit_on_rank0": ok, "gpu_launches": args.steps * 2}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
-    if args.lookback_share:
+    if args.split:
+        run_split(args)
+    elif args.lookback_share:
         lookback_share(args)
     elif args.table1:
         table1(args)

@@ -61,3 +61,25 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(args)
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch):
+    # the reference arm's JSON line on a tiny stand-in workload: the oracle
+    # on host threads, the GPU arm's config, no host-device copies
+    sys.path.insert(0, ROOT)
+    import json
+
+    import bench
+    monkeypatch.setattr(bench, "N_MAIN", 2**16)
+    monkeypatch.setattr(bench, "REF_DOMAIN_SAMPLE", 2**12)
+    monkeypatch.setenv("RANK", "0")
+    args = bench.argparse.Namespace(gpus=1, steps=3, warmup=1)
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(args)
+    line = json.loads(buf.getvalue().strip())
+    assert line["impl"] == "reference" and line["steps"] == 3 and line["warmup"] == 1
+    assert line["config"] == bench.workload_config(1)
+    assert line["metric"] == bench.METRIC and line["unit"] == "elements/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
