@@ -17,7 +17,8 @@ Printed on one JSON line (rank 0):
                HBM copy peak, with its DRAM traffic from the committed ncu
                record while the kernel source is unchanged
   e2e          the same metric through the C ABI from pinned host buffers,
-               host-to-device and device-to-host copies inside the timed region
+               host-to-device and device-to-host copies inside the timed region,
+               with the copies alone timed beside it (the host link's floor)
   cpu_baseline the CPU oracle, as it stands, on a bounded sample of the same
                workload (the first slots of the same shuffle)
   extra        every strategy at n = 2^28 and at the worst-case padding
@@ -510,6 +511,8 @@ def summary(line: dict) -> dict:
                                      "oracle_1_thread": cpu["single_thread"]["value"],
                                      "fisher_yates": cpu["fisher_yates"]["value"]}
     out["e2e_elements_per_s"] = line["e2e"]["value"]
+    if "frac_of_copy_floor" in line["e2e"]:
+        out["e2e_frac_of_copy_floor"] = round(line["e2e"]["frac_of_copy_floor"], 3)
     return out
 
 
@@ -609,10 +612,27 @@ def e2e_pipeline(bs, torch, dev, host, seed, args, world):
     e1.record(s_out)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1), world)
+    # The copy floor: the same copies alone, both directions at once (the
+    # host link, not the shuffle, bounds the end-to-end rate).
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c0.record(s_in)
+    s_out.wait_event(c0)
+    for i in range(steps):
+        with torch.cuda.stream(s_in):
+            xs[i % 2].copy_(hin, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            hout.copy_(ys[i % 2], non_blocking=True)
+    s_out.wait_stream(s_in)
+    c1.record(s_out)
+    torch.cuda.synchronize()
+    floor_ms = max_over_ranks(c0.elapsed_time(c1), world) / steps
     del xs, ys, hin, hout
     return {"value": N_MAIN * world * steps / (ms * 1e-3), "unit": "elements/s",
             "h2d_bytes_per_step": N_MAIN * ELEM, "d2h_bytes_per_step": N_MAIN * ELEM,
             "ms_per_step": ms / steps, "steps": steps,
+            "copy_floor_ms_per_step": floor_ms, "frac_of_copy_floor": floor_ms / (ms / steps),
             "pipeline": "copy-in, shuffle and copy-out of consecutive steps overlap on three streams"}
 
 
