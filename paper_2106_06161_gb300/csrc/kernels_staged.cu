@@ -69,15 +69,6 @@ constexpr uint32_t kP1TileSmall = kP1Block * 8;
 constexpr uint32_t kP1TileLarge = kP1Block * 16;
 constexpr uint32_t kStagedMinChunk = kP1TileSmall > kSTile ? kP1TileSmall : kSTile;
 constexpr uint32_t kMinWindowLog2 = 22;       // 4 MiB
-// Elements of a P1 chunk per destination bucket (the bucket count is the
-// chunk size over this), for 4- and 8-byte and for 16-byte elements
-// (overridable at build time for tuning experiments).
-#ifndef BSHUFFLE_STAGED_CHUNK_PER_BUCKET
-#define BSHUFFLE_STAGED_CHUNK_PER_BUCKET 8
-#endif
-#ifndef BSHUFFLE_STAGED_CHUNK_PER_BUCKET_16B
-#define BSHUFFLE_STAGED_CHUNK_PER_BUCKET_16B 8
-#endif
 constexpr uint64_t kLargeInputBytes = uint64_t{1} << 31;  // above this, 16 items per P1 thread
 
 // P1 items per thread for n elements of elem_bytes.
@@ -647,10 +638,8 @@ uint32_t staged_window_shift(uint64_t n, uint32_t elem_bytes)
     uint32_t eb_log2 = 0;
     while ((1u << eb_log2) < elem_bytes) ++eb_log2;
     // one bucket per 8 elements of a P1 chunk: 256 (or 512) buckets
-    const uint32_t per_bucket =
-        elem_bytes == 16 ? BSHUFFLE_STAGED_CHUNK_PER_BUCKET_16B : BSHUFFLE_STAGED_CHUNK_PER_BUCKET;
     uint32_t bucket_log2 = 0;
-    while ((per_bucket << bucket_log2) < static_cast<uint32_t>(kP1Block) * p1_items_for(n, elem_bytes)) ++bucket_log2;
+    while ((8u << bucket_log2) < static_cast<uint32_t>(kP1Block) * p1_items_for(n, elem_bytes)) ++bucket_log2;
     uint32_t shift = lg > bucket_log2 ? lg - bucket_log2 : 0u;
     const uint32_t min_shift = kMinWindowLog2 > eb_log2 ? kMinWindowLog2 - eb_log2 : 0u;
     if (shift < min_shift) shift = min_shift;
