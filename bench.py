@@ -855,7 +855,8 @@ def table1(args):
     """Tables 1 and 2 of Sec. 6 on this GPU: millions of 64-bit keys shuffled
     per second at the worst-case lengths 2^w + 1, for the random-gather bound
     (2^w elements: the measurement kernel takes powers of two), the library's
-    default shuffle (pipelined single pass for these lengths), the paper's
+    default shuffle (the ranked staged form from 256 MiB of input, single-pass
+    kernels below), the paper's
     fused single pass (Bijective2) and the LCG bijection through the same
     kernel.  Every launch reuses the same buffers, so lengths up to about
     2^23 stay resident in the 129 MB L2 between launches."""
