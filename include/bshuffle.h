@@ -165,6 +165,8 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
  *   aligned, caller-owned) = the number of i in [first, end) with f(i) < n,
  *   on the domain of n (end is clipped to 2^k).  The count is written
  *   asynchronously on `stream` (it is zeroed first, then the GPU adds to it).
+ *   For n = 2^k (k >= 4) nothing is dropped and the count is end - first,
+ *   stored without evaluating the cipher.
  *   BSHUFFLE_ERR_INVALID if first > end.  No workspace.
  * bshuffle_permute_range: out[t] = in[f(i_t)] for the t-th kept domain index
  *   i_t in [first, end), in increasing order (t < the count above).  in holds
@@ -173,7 +175,10 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
  *   A slot at or past out_capacity is not written and records
  *   BSHUFFLE_ERR_DEVICE_BOUNDS.  elem_bytes 1, 2, 4, 8 or 16; first < 2^32.
  *   Uses the stream's workspace (one status word per 2,048 indices of the
- *   range) and the fused single pass; errors as for bshuffle_permute.
+ *   range) and the fused single pass; for n = 2^k (16 <= n <= 2^31) the scan
+ *   over the range is the identity, so the scan-free gather runs instead
+ *   (out[t] = in[f(first + t)], the workspace's error word only).  Errors as
+ *   for bshuffle_permute.
  */
 int bshuffle_count_range(uint64_t n, uint64_t seed, uint32_t rounds, uint64_t first, uint64_t end,
                          uint64_t *d_count, void *stream);

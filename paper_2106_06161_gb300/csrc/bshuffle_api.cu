@@ -612,6 +612,11 @@ int bshuffle_count_range(uint64_t n, uint64_t seed, uint32_t rounds, uint64_t fi
     const Geometry g = geometry_of(n);
     if (end > g.domain) end = g.domain;
     if (first >= end) return BSHUFFLE_OK;
+    if (g.domain == n) {
+        // n = 2^k: nothing is dropped, the count is the range's length
+        e = bsh::launch_store_count(reinterpret_cast<unsigned long long *>(d_count), end - first, stream);
+        return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
+    }
     uint32_t keys[BSHUFFLE_MAX_ROUNDS];
     fill_keys(seed, rounds, keys);
     e = bsh::launch_count_range(g, keys, rounds, first, end, reinterpret_cast<unsigned long long *>(d_count),
@@ -652,15 +657,20 @@ int bshuffle_permute_range(const void *in, void *out, uint64_t n, uint32_t elem_
     a.skip_publish_tile = g_skip_publish.load();
     a.timeout_ns = g_timeout_ns.load();
     fill_keys(seed, rounds, a.keys);
+    // n = 2^k: every index is kept, the scan over the range is the identity,
+    // and the scan-free gather serves the range (the workspace only takes its
+    // error word)
+    const bool direct = g.domain == n && n >= 16 && n <= (uint64_t{1} << 31);
     const uint64_t tile = bsh::elem_tile_size(0);
-    const uint64_t tiles = (end - first + tile - 1) / tile;
+    const uint64_t tiles = direct ? 1 : (end - first + tile - 1) / tile;
     a.num_tiles = static_cast<uint32_t>(tiles);
     Workspace *ws = nullptr;
     rc = acquire_workspace(stream, tiles, &ws);
     if (rc != BSHUFFLE_OK) return rc;
     a.ws = ws->header();
     a.status = ws->status();
-    const cudaError_t e = bsh::launch_permute_range(a, elem_bytes, stream);
+    const cudaError_t e = direct ? bsh::launch_direct_range(a, elem_bytes, stream)
+                                 : bsh::launch_permute_range(a, elem_bytes, stream);
     return e == cudaSuccess ? BSHUFFLE_OK : cuda_fail(e);
 }
 

@@ -119,6 +119,13 @@ cudaError_t launch_rows(const TileArgs &a, Mode mode, cudaStream_t stream);
 // which is the identity when nothing is dropped.  Every mode; elem_bytes 1,
 // 2, 4, 8, 16 or rows of a multiple of 16 bytes.
 cudaError_t launch_direct(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream);
+// The gather of the domain range [range_first, range_end) of a power-of-two
+// length (n <= 2^31) into out[0 .. range_end - range_first), bounded by
+// range_cap; no workspace, no scan.  elem_bytes 1, 2, 4, 8 or 16.
+cudaError_t launch_direct_range(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream);
+// Writes `value` into *count on `stream` (the count of a range of a
+// power-of-two length: its length).
+cudaError_t launch_store_count(unsigned long long *count, uint64_t value, cudaStream_t stream);
 
 // ------------------------------------------------------------------ batched
 

@@ -81,6 +81,44 @@ __global__ void __launch_bounds__(kDBlock) direct_elem_kernel(const __grid_const
     }
 }
 
+// The gather restricted to the domain range [range_first, range_end) of a
+// power-of-two length: every index is kept, so the range's t-th index
+// range_first + t fills out[t] (the exclusive scan over the range is the
+// identity too).  A slot at or past range_cap is not written and records a
+// bounds error.
+template <class T, bool ODD>
+__global__ void __launch_bounds__(kDBlock) direct_range_kernel(const __grid_constant__ TileArgs a)
+{
+    const uint32_t n = a.g.n;  // == 2^k <= 2^31
+    const uint64_t len = a.range_end - a.range_first;
+    const uint64_t t0 = uint64_t{blockIdx.x} * (kDBlock * kDItems) + threadIdx.x;
+    uint32_t i[kDItems], f[kDItems];
+#pragma unroll
+    for (int j = 0; j < kDItems; ++j) {
+        const uint64_t t = t0 + static_cast<uint64_t>(j * kDBlock);
+        i[j] = t < len ? a.range_first + static_cast<uint32_t>(t) : 0u;
+    }
+    images<ODD, kDItems>(a, i, f);
+    const T *in = static_cast<const T *>(a.in);
+    T *out = static_cast<T *>(a.out);
+    T v[kDItems];
+#pragma unroll
+    for (int j = 0; j < kDItems; ++j) {
+        const uint64_t t = t0 + static_cast<uint64_t>(j * kDBlock);
+        if (t < len && t < a.range_cap && f[j] < n) v[j] = __ldg(in + f[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kDItems; ++j) {
+        const uint64_t t = t0 + static_cast<uint64_t>(j * kDBlock);
+        if (t >= len) continue;
+        if (t >= a.range_cap || f[j] >= n) {  // f[j] >= n is impossible for a bijection; kept as a guard
+            dev::record_error(a.ws, dev::kErrDeviceBounds, t);
+            continue;
+        }
+        out[t] = v[j];
+    }
+}
+
 template <Mode MODE, bool ODD>
 __global__ void __launch_bounds__(kDBlock) direct_rows_kernel(const __grid_constant__ TileArgs a)
 {
@@ -186,7 +224,34 @@ cudaError_t launch_by_width(const TileArgs &a, uint32_t elem_bytes, cudaStream_t
     }
 }
 
+template <class T>
+cudaError_t launch_range_t(const TileArgs &a, cudaStream_t stream)
+{
+    const uint64_t per_cta = kDBlock * kDItems;
+    const uint64_t blocks = (a.range_end - a.range_first + per_cta - 1) / per_cta;
+    if (blocks == 0) return cudaSuccess;
+    const dim3 grid(static_cast<unsigned>(blocks)), block(kDBlock);
+    if (a.g.k & 1u) direct_range_kernel<T, true><<<grid, block, 0, stream>>>(a);
+    else direct_range_kernel<T, false><<<grid, block, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_direct_range(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream)
+{
+    if (a.g.domain != a.g.n || a.g.n < 16u || a.g.n > (uint64_t{1} << 31) || a.range_end > a.g.domain ||
+        a.range_first > a.range_end)
+        return cudaErrorInvalidValue;
+    switch (elem_bytes) {
+    case 1: return launch_range_t<unsigned char>(a, stream);
+    case 2: return launch_range_t<unsigned short>(a, stream);
+    case 4: return launch_range_t<unsigned int>(a, stream);
+    case 8: return launch_range_t<unsigned long long>(a, stream);
+    case 16: return launch_range_t<uint4>(a, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_direct(const TileArgs &a, Mode mode, uint32_t elem_bytes, cudaStream_t stream)
 {

@@ -8,7 +8,9 @@
 // indices (count_range_kernel: the cipher and the keep test, no memory
 // traffic), the counts are scanned in range order, and every part gathers its
 // range's kept elements into its run of slots (the fused single pass
-// restricted to the range, elem_tile_kernel with RANGE).
+// restricted to the range, elem_tile_kernel with RANGE).  For n = 2^k nothing
+// is dropped: a range's count is its length, and its gather is the scan-free
+// direct_range_kernel (kernels_direct.cu).
 #include <cstdint>
 
 #include "bshuffle_device.cuh"
@@ -55,6 +57,8 @@ __global__ void __launch_bounds__(kCountBlock) count_range_kernel(const __grid_c
     if ((threadIdx.x & 31u) == 0 && kept != 0u) atomicAdd(a.count, static_cast<unsigned long long>(kept));
 }
 
+__global__ void store_count_kernel(unsigned long long *count, unsigned long long value) { *count = value; }
+
 template <class T>
 cudaError_t launch_range_typed(const TileArgs &a, cudaStream_t stream)
 {
@@ -82,6 +86,12 @@ cudaError_t launch_permute_range(const TileArgs &a, uint32_t elem_bytes, cudaStr
     case 16: return launch_range_typed<uint4>(a, stream);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_store_count(unsigned long long *count, uint64_t value, cudaStream_t stream)
+{
+    store_count_kernel<<<1, 1, 0, stream>>>(count, static_cast<unsigned long long>(value));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_count_range(const Geometry &g, const uint32_t *keys, uint32_t rounds, uint64_t first,

@@ -13,6 +13,10 @@ the ranges before it.  Each rank therefore
   3. gathers its range's kept elements from the whole input, which every rank
      holds (bshuffle_permute_range), into its part of the output.
 
+For n = 2^k (k >= 4) no domain index is dropped: a range's count is its
+length and its offset is its first index, so the ranks need no exchange at
+all, and each gathers its range with the scan-free kernel.
+
 Every step of the shuffle runs in the library's kernels; this module only
 plans the ranges and moves the counts between ranks.
 """
@@ -76,7 +80,9 @@ def permute_shard(x: torch.Tensor, seed: int, rank: int, world: int, rounds: int
     the shuffled output, offset).  x (CUDA, rows along dim 0 of 1, 2, 4, 8 or
     16 bytes) is the whole input on every rank.  With exchange=False the
     counts of the ranges before this one are recomputed on this GPU instead of
-    being all-gathered (no communication; the count reads no data)."""
+    being all-gathered (no communication; the count reads no data).  For
+    n = 2^k (n >= 16) the counts are the ranges' lengths and nothing is
+    exchanged either way."""
     if not x.is_cuda:
         raise ValueError("permute_shard needs a CUDA tensor")
     x = x.contiguous()
@@ -84,7 +90,9 @@ def permute_shard(x: torch.Tensor, seed: int, rank: int, world: int, rounds: int
     elem = x.element_size() * (x.numel() // n if n else 1)
     parts = ranges(n, world)
     first, end = parts[rank]
-    if exchange:
+    if n >= 16 and n & (n - 1) == 0:
+        offset, count = first, end - first
+    elif exchange:
         mine = count_range(n, seed, first, end, rounds, x.device)
         offset, _, counts = exchange_counts(mine, group)
         count = counts[rank]

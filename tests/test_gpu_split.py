@@ -131,3 +131,59 @@ def test_capacity_bounds_the_writes(bs):
     want = oracle.indices(n, seed)[:100].astype(np.int64)
     assert np.array_equal(out[:100].cpu().numpy(), want)
     assert bool((out[100:] == -1).all())
+
+
+@pytest.mark.parametrize("width", [1, 2, 4, 8, 16])
+def test_power_of_two_ranges_scan_free(bs, width):
+    # n = 2^k: every domain index is kept, so a range's count is its length,
+    # its t-th slot holds x[f(first + t)], and the scan-free gather serves it;
+    # ranges off the 2,048-index grid, empty, and clipped past the domain
+    stream = torch.cuda.current_stream().cuda_stream
+    n, seed = 2**17, 9
+    x = _payload(n, width, seed)
+    xd = to_device(x)
+    idx = oracle.indices(n, seed).astype(np.int64)
+    c_dev = torch.empty(1, dtype=torch.int64, device="cuda")
+    bounds = [0, 1, 2047, 2049, 50_001, 50_001, 131_071, 2**40]
+    for f, e in zip(bounds[:-1], bounds[1:]):
+        bs.bshuffle_count_range(n, seed, 24, f, e, c_dev.data_ptr(), stream)
+        c = int(c_dev.item())
+        assert c == min(e, n) - f == oracle.count_range(n, seed, f, e), (f, e)
+        if not c:
+            continue
+        out = to_device(np.zeros_like(x[:c]))
+        bs.bshuffle_permute_range(xd.data_ptr(), out.data_ptr(), n, width, seed, 24, f, e, c, stream)
+        assert_no_device_error()
+        assert np.array_equal(to_host(out, x[:c]), x[idx[f:f + c]]), (f, e)
+
+
+def test_power_of_two_capacity_bounds_the_writes(bs):
+    from paper_2106_06161_gb300 import _lib as L
+    n, seed = 2**14, 4
+    x = torch.arange(n, dtype=torch.int64, device="cuda")
+    out = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    bs.bshuffle_permute_range(x.data_ptr(), out.data_ptr(), n, 8, seed, 24, 100, n, 1000, s)
+    torch.cuda.synchronize()
+    assert bs.get_error() == L.BSHUFFLE_ERR_DEVICE_BOUNDS
+    want = oracle.indices(n, seed)[100:1100].astype(np.int64)
+    assert np.array_equal(out[:1000].cpu().numpy(), want)
+    assert bool((out[1000:] == -1).all())
+    # the next call on the stream is exact again
+    bs.bshuffle_permute_range(x.data_ptr(), out.data_ptr(), n, 8, seed, 24, 0, n, n, s)
+    assert_no_device_error()
+    assert np.array_equal(out.cpu().numpy(), oracle.indices(n, seed).astype(np.int64))
+
+
+def test_power_of_two_shards_need_no_exchange(bs):
+    from paper_2106_06161_gb300 import split
+    n, seed = 2**22, 12
+    x = workloads.uniform_u64(n, seed)
+    xd = to_device(x)
+    want = oracle.permute_mt(x, seed)
+    for world in (2, 3, 4):
+        pieces = [split.permute_shard(xd, seed, r, world) for r in range(world)]
+        assert_no_device_error()
+        assert [p[1] for p in pieces] == [f for f, _ in split.ranges(n, world)]
+        got = torch.cat([p[0] for p in pieces])
+        assert np.array_equal(to_host(got, x), want)
