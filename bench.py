@@ -505,6 +505,8 @@ def summary(line: dict) -> dict:
     b = ex.get("batched_4096_uneven_int32")
     if b:
         out["batched_speedup"] = round(b["speedup"], 2)
+        if "speedup_vs_graph" in b:
+            out["batched_speedup_vs_graph"] = round(b["speedup_vs_graph"], 2)
     cpu = line.get("cpu_baseline")
     if cpu:
         out["cpu_elements_per_s"] = {"oracle_threads": cpu["value"], "cores": cpu["cores"],
@@ -799,10 +801,32 @@ def secondary(bs, torch, dev, stream):
     torch.cuda.synchronize()
     _, tp = timed_launches(plain_all, 3, stream, torch)
     same = bool(torch.equal(res, batched_ref))
+    # the same 4096 launches captured once in a CUDA graph: their GPU-side
+    # time without the host's per-call cost (the first pass on the capture
+    # stream sizes its workspace)
+    gs = torch.cuda.Stream(dev)
+    gptr = gs.cuda_stream
+    with torch.cuda.stream(gs):
+        for t in range(count):
+            bs.bshuffle_permute(ins[t], outs[t], ns[t], 4, t, ROUNDS, gptr)
+        gs.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            for t in range(count):
+                bs.bshuffle_permute(ins[t], outs[t], ns[t], 4, t, ROUNDS, gptr)
+    torch.cuda.synchronize()
+    res.zero_()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    same_graph = bool(torch.equal(res, batched_ref))
+    _, tg = timed_launches(graph.replay, 3, stream, torch)
+    del graph
     out["batched_4096_uneven_int32"] = {
         "batched_ms": tb / 10, "plain_ms": tp / 3, "speedup": (tp / 3) / (tb / 10),
+        "plain_graph_ms": tg / 3, "speedup_vs_graph": (tg / 3) / (tb / 10),
         "batched_shuffles_per_s": count / (tb / 10 * 1e-3), "plain_shuffles_per_s": count / (tp / 3 * 1e-3),
-        "total_elements": int(sizes.sum()), "batched_equals_plain": same,
+        "total_elements": int(sizes.sum()), "batched_equals_plain": same, "graph_equals_batched": same_graph,
         "batched_ms_default_shape": by_config[0], "batched_ms_tuned_shape": by_config[tuned],
         "tuned_config": tuned}
     return out
