@@ -175,7 +175,8 @@ int bshuffle_batched(const bshuffle_desc *d_descs, uint32_t count, uint32_t elem
  *   A slot at or past out_capacity is not written and records
  *   BSHUFFLE_ERR_DEVICE_BOUNDS.  elem_bytes 1, 2, 4, 8 or 16; first < 2^32.
  *   Uses the stream's workspace (one status word per 2,048 indices of the
- *   range) and the fused single pass; for n = 2^k (16 <= n <= 2^31) the scan
+ *   range) and the fused single pass (pipelined for 4-, 8- and 16-byte
+ *   elements, as in bshuffle_permute); for n = 2^k (16 <= n <= 2^31) the scan
  *   over the range is the identity, so the scan-free gather runs instead
  *   (out[t] = in[f(first + t)], the workspace's error word only).  Errors as
  *   for bshuffle_permute.

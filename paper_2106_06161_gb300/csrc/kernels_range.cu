@@ -8,7 +8,8 @@
 // indices (count_range_kernel: the cipher and the keep test, no memory
 // traffic), the counts are scanned in range order, and every part gathers its
 // range's kept elements into its run of slots (the fused single pass
-// restricted to the range, elem_tile_kernel with RANGE).  For n = 2^k nothing
+// restricted to the range: the pipelined kernel with RANGE for 4-, 8- and
+// 16-byte elements, elem_tile_kernel with RANGE for 1 and 2 bytes).  For n = 2^k nothing
 // is dropped: a range's count is its length, and its gather is the scan-free
 // direct_range_kernel (kernels_direct.cu).
 #include <cstdint>
@@ -16,6 +17,7 @@
 #include "bshuffle_device.cuh"
 #include "bshuffle_internal.h"
 #include "elem_kernel.cuh"
+#include "pipe_kernel.cuh"
 
 namespace bsh {
 namespace {
@@ -77,13 +79,15 @@ cudaError_t launch_range_typed(const TileArgs &a, cudaStream_t stream)
 
 cudaError_t launch_permute_range(const TileArgs &a, uint32_t elem_bytes, cudaStream_t stream)
 {
-    if (elem_tile_size(0) != 256u * 8u) return cudaErrorInvalidValue;  // tiles as counted by the caller
+    // tiles as counted by the caller: 2,048 domain indices (the plain
+    // kernel's 256 x 8 and the pipelined kernel's 8 warps x 32 x 8)
+    if (elem_tile_size(0) != 256u * 8u || pipe_tile_size(elem_bytes, 0) != 256u * 8u) return cudaErrorInvalidValue;
     switch (elem_bytes) {
     case 1: return launch_range_typed<uint8_t>(a, stream);
     case 2: return launch_range_typed<uint16_t>(a, stream);
-    case 4: return launch_range_typed<uint32_t>(a, stream);
-    case 8: return launch_range_typed<unsigned long long>(a, stream);
-    case 16: return launch_range_typed<uint4>(a, stream);
+    case 4: return pipe::launch_shape<uint32_t, Mode::Gather, 8, 8, 3, true, true>(a, stream);
+    case 8: return pipe::launch_shape<unsigned long long, Mode::Gather, 8, 8, 3, true, true>(a, stream);
+    case 16: return pipe::launch_shape<uint4, Mode::Gather, 8, 8, 3, true, true>(a, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -66,7 +66,10 @@ using PipeSlot = typename std::conditional<MODE == Mode::Scatter, uint32_t, T>::
 
 // MINB: resident CTAs per SM the register budget targets; UNROLL: the
 // default round count runs fully unrolled (else every count runs in a loop).
-template <class T, Mode MODE, bool ODD, int NCW, int ITEMS, int MINB, bool UNROLL>
+// RANGE: Algorithm 1 restricted to the domain indices [range_first,
+// range_end) (tiles counted from range_first), writing the range's kept
+// elements to out[0 .. count), at most range_cap of them.
+template <class T, Mode MODE, bool ODD, int NCW, int ITEMS, int MINB, bool UNROLL, bool RANGE = false>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const __grid_constant__ TileArgs a)
 {
     using S = PipeSlot<T, MODE>;
@@ -82,6 +85,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const _
     const uint32_t warp = threadIdx.x >> 5;
     // a wait for the other role gets room for one full look-back timeout
     const uint64_t role_limit = 2 * a.timeout_ns + 1000000000ull;
+    // slots a range launch may write
+    const uint32_t range_limit = RANGE && a.range_cap < a.g.n ? static_cast<uint32_t>(a.range_cap) : a.g.n;
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
@@ -110,7 +115,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const _
             const uint32_t tile = sh.ticket[b];
             const bool stop = tile >= a.num_tiles;
             if (!stop) {
-                const uint32_t base = tile * TILE;
+                const uint32_t base = (RANGE ? a.range_first : 0u) + tile * TILE;
                 uint32_t left[ITEMS], right[ITEMS];
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) {
@@ -128,7 +133,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const _
                 for (int j = 0; j < ITEMS; ++j) {
                     const uint32_t i = base + static_cast<uint32_t>(j) * NCT + ct;
                     const uint32_t src = (left[j] << a.g.R) | right[j];
-                    const bool keep = static_cast<uint64_t>(i) < a.g.domain && src < a.g.n;
+                    bool in_domain;
+                    if constexpr (RANGE)
+                        in_domain = uint64_t{a.range_first} + uint64_t{tile} * TILE + static_cast<uint32_t>(j) * NCT +
+                                        ct <
+                                    a.range_end;
+                    else
+                        in_domain = static_cast<uint64_t>(i) < a.g.domain;
+                    const bool keep = in_domain && src < a.g.n;
                     if (keep) {
                         S *slot = buf + static_cast<uint32_t>(j) * NCT + ct;
                         if constexpr (MODE == Mode::Gather)
@@ -194,7 +206,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const _
                             const uint32_t m = sh.masks[pb][e];
                             if ((m >> lane) & 1u) {
                                 const uint32_t dst = prefix + sh.offs[pb][e] + __popc(m & lt);
-                                if (dst < a.g.n) out[dst] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
+                                if (RANGE ? dst < range_limit : dst < a.g.n)
+                                    out[dst] = pbuf[static_cast<uint32_t>(j) * NCT + ct];
                                 else dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
                             }
                         }
@@ -266,7 +279,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) pipe_tile_kernel(const _
 
 // Launch one shape: persistent CTAs, as many as fit on the device (cached
 // per device and parity on first use), never more than the tiles.
-template <class T, Mode MODE, int NCW, int ITEMS, int MINB, bool UNROLL>
+template <class T, Mode MODE, int NCW, int ITEMS, int MINB, bool UNROLL, bool RANGE = false>
 cudaError_t launch_shape(const TileArgs &a, cudaStream_t stream)
 {
     constexpr int THREADS = (NCW + 1) * 32;
@@ -277,8 +290,8 @@ cudaError_t launch_shape(const TileArgs &a, cudaStream_t stream)
     if (e != cudaSuccess) return e;
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     const bool odd = (a.g.k & 1u) != 0u;
-    auto kernel = odd ? pipe_tile_kernel<T, MODE, true, NCW, ITEMS, MINB, UNROLL>
-                      : pipe_tile_kernel<T, MODE, false, NCW, ITEMS, MINB, UNROLL>;
+    auto kernel = odd ? pipe_tile_kernel<T, MODE, true, NCW, ITEMS, MINB, UNROLL, RANGE>
+                      : pipe_tile_kernel<T, MODE, false, NCW, ITEMS, MINB, UNROLL, RANGE>;
     std::atomic<int> &slot = per_sm[device][odd ? 1 : 0];
     int ctas = slot.load(std::memory_order_acquire);
     if (ctas == 0) {
