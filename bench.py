@@ -615,26 +615,32 @@ def e2e_pipeline(bs, torch, dev, host, seed, args, world):
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     # The copy floor: the same copies alone, both directions at once (the
-    # host link, not the shuffle, bounds the end-to-end rate).
-    c0 = torch.cuda.Event(enable_timing=True)
-    c1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    c0.record(s_in)
-    s_out.wait_event(c0)
-    for i in range(steps):
-        with torch.cuda.stream(s_in):
-            xs[i % 2].copy_(hin, non_blocking=True)
-        with torch.cuda.stream(s_out):
-            hout.copy_(ys[i % 2], non_blocking=True)
-    s_out.wait_stream(s_in)
-    c1.record(s_out)
-    torch.cuda.synchronize()
-    floor_ms = max_over_ranks(c0.elapsed_time(c1), world) / steps
+    # host link, not the shuffle, bounds the end-to-end rate); the best of
+    # three trials, since the host link is shared with the machine's other
+    # GPUs and a transfer of theirs slows a trial down.
+    trials = []
+    for _ in range(3):
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        c0.record(s_in)
+        s_out.wait_event(c0)
+        for i in range(steps):
+            with torch.cuda.stream(s_in):
+                xs[i % 2].copy_(hin, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                hout.copy_(ys[i % 2], non_blocking=True)
+        s_out.wait_stream(s_in)
+        c1.record(s_out)
+        torch.cuda.synchronize()
+        trials.append(max_over_ranks(c0.elapsed_time(c1), world) / steps)
+    floor_ms = min(trials)
     del xs, ys, hin, hout
     return {"value": N_MAIN * world * steps / (ms * 1e-3), "unit": "elements/s",
             "h2d_bytes_per_step": N_MAIN * ELEM, "d2h_bytes_per_step": N_MAIN * ELEM,
             "ms_per_step": ms / steps, "steps": steps,
-            "copy_floor_ms_per_step": floor_ms, "frac_of_copy_floor": floor_ms / (ms / steps),
+            "copy_floor_ms_per_step": floor_ms, "copy_floor_trials_ms": trials,
+            "frac_of_copy_floor": floor_ms / (ms / steps),
             "pipeline": "copy-in, shuffle and copy-out of consecutive steps overlap on three streams"}
 
 
