@@ -103,3 +103,39 @@ def test_largest_staged_length(bs):
         bs.bshuffle_set_strategy(bs.BSHUFFLE_STRATEGY_AUTO)
     del x, y, z
     torch.cuda.empty_cache()
+
+
+def test_max_length_ranges(bs):
+    # the range entry points at the largest length: ranges at the start, the
+    # middle and the top of the 2^32 domain (where a tile's 32-bit base
+    # passes 2^32), 4-byte elements through the pipelined range kernel and
+    # 1-byte elements through the plain one
+    seed = 23
+    keys = oracle.round_keys(seed, 24)
+    s = torch.cuda.current_stream().cuda_stream
+    c_dev = torch.empty(1, dtype=torch.int64, device="cuda")
+    ranges = ((0, 2**20 + 3), (2**31 - 1000, 2**31 + 1000), (2**32 - 2**20 - 5, 2**32))
+    expected = []
+    for first, end in ranges:
+        f = oracle.varphilox(np.arange(first, end, dtype=np.uint64), 32, keys)
+        kept = f[f < N_MAX]
+        assert kept.size == oracle.count_range(N_MAX, seed, first, end)
+        bs.bshuffle_count_range(N_MAX, seed, 24, first, end, c_dev.data_ptr(), s)
+        assert int(c_dev.item()) == kept.size, (first, end)
+        expected.append(kept)
+    x = torch.arange(N_MAX, dtype=torch.int64, device="cuda").to(torch.int32)  # x[b] = b
+    for (first, end), kept in zip(ranges, expected):
+        out = torch.full((kept.size,), -1, dtype=torch.int32, device="cuda")
+        bs.bshuffle_permute_range(x.data_ptr(), out.data_ptr(), N_MAX, 4, seed, 24, first, end, kept.size, s)
+        assert_no_device_error()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32).astype(np.uint64), kept), (first, end)
+    del x
+    torch.cuda.empty_cache()
+    x8 = torch.arange(256, dtype=torch.uint8, device="cuda").repeat(N_MAX // 256 + 1)[:N_MAX].contiguous()
+    for (first, end), kept in zip(ranges, expected):
+        out = torch.empty(kept.size, dtype=torch.uint8, device="cuda")
+        bs.bshuffle_permute_range(x8.data_ptr(), out.data_ptr(), N_MAX, 1, seed, 24, first, end, kept.size, s)
+        assert_no_device_error()
+        assert np.array_equal(out.cpu().numpy(), (kept & np.uint64(255)).astype(np.uint8)), (first, end)
+    del x8
+    torch.cuda.empty_cache()
