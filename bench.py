@@ -1008,6 +1008,7 @@ def run_split(args):
     region_ms = max_over_ranks(e0.elapsed_time(e1), world)
     whole = bs.permute(x, SEED, ROUNDS)
     ok = bool(torch.equal(whole[offset:offset + part.shape[0]], part))
+    emulated = emulated_ranks(bs, split, torch, stream) if world == 1 else None
     if rank == 0:
         ms = region_ms / args.steps
         line = {"metric": METRIC, "value": N_MAIN * args.steps / (region_ms * 1e-3), "unit": "elements/s",
@@ -1018,10 +1019,57 @@ def run_split(args):
                                                                   f"{world} GPU(s); n = 2^k keeps every index, "
                                                                   f"so no exchange"),
                 "split_equals_unsplit_on_rank0": ok, "gpu_launches": args.steps}
+        if emulated is not None:
+            line["emulated_ranks"] = emulated
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def emulated_ranks(bs, split, torch, stream, reps=5):
+    """Each rank's own work at P ranks, measured part by part on this GPU: its
+    range count (not for n = 2^k), the host read of the count, and its range
+    gather from the whole input, as one rank would run them alone on its own
+    GPU; the slowest part bounds a step at P GPUs, the all-gather of the
+    counts aside.  Every part's output is checked against the unsplit
+    shuffle."""
+    sptr = stream.cuda_stream
+    out = {}
+    for n in (N_MAIN, N_MAIN + 12345):
+        x = torch.from_numpy(workloads.uniform_u64(n, SEED).view(np.int64)).cuda()
+        whole = bs.permute(x, SEED, ROUNDS)
+        y = torch.empty_like(x)
+        pow2 = n & (n - 1) == 0
+        rows, exact = {}, True
+        for parts in (1, 2, 4, 8):
+            ranges = split.ranges(n, parts)
+            offset, times = 0, []
+            for first, end in ranges:
+                def work(first=first, end=end):
+                    count = end - first if pow2 else int(split.count_range(n, SEED, first, end, ROUNDS).item())
+                    bs.bshuffle_permute_range(x.data_ptr(), y.data_ptr(), n, ELEM, SEED, ROUNDS, first, end, count,
+                                              sptr)
+                    return count
+                count = work()
+                torch.cuda.synchronize()
+                exact = exact and bool(torch.equal(y[:count], whole[offset:offset + count]))
+                offset += count
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    work()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / reps)
+            exact = exact and offset == n
+            rows[str(parts)] = {"max_part_ms": max(times), "parts_ms": times}
+        if bs.get_error() != 0:
+            raise SystemExit("device error")
+        out["2^28" if pow2 else "2^28+12345"] = {"parts_equal_unsplit": exact, "by_parts": rows}
+        del x, y, whole
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
