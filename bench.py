@@ -889,7 +889,9 @@ def table1(args):
     kernels below), the paper's
     fused single pass (Bijective2) and the LCG bijection through the same
     kernel.  Every launch reuses the same buffers, so lengths up to about
-    2^23 stay resident in the 129 MB L2 between launches."""
+    2^23 stay resident in the 129 MB L2 between launches.  varphilox_graph is
+    the default shuffle's calls replayed from a CUDA graph (no host cost per
+    call)."""
     import torch
     from paper_2106_06161_gb300 import build as bsbuild
     bsbuild.build()
@@ -916,6 +918,23 @@ def table1(args):
                 fn()
             _, region = timed_launches(fn, reps, stream, torch)
             row[name] = items * reps / (region * 1e-3) / 1e6
+        # the default shuffle's calls replayed from one CUDA graph: the GPU's
+        # rate without the per-call cost of a call from Python (the first
+        # call on the capture stream creates its workspace)
+        gcalls = min(reps, 200)
+        gs = torch.cuda.Stream()
+        with torch.cuda.stream(gs):
+            bs.bshuffle_permute(xp, yp, n, ELEM, w, ROUNDS, gs.cuda_stream)
+            gs.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=gs):
+                for _ in range(gcalls):
+                    bs.bshuffle_permute(xp, yp, n, ELEM, w, ROUNDS, gs.cuda_stream)
+        torch.cuda.synchronize()
+        graph.replay()
+        _, gregion = timed_launches(graph.replay, 3, stream, torch)
+        row["varphilox_graph"] = n * gcalls * 3 / (gregion * 1e-3) / 1e6
+        del graph
         if bs.get_error() != 0:
             raise SystemExit("device error")
         rows[f"2^{w}+1"] = row
