@@ -571,7 +571,7 @@ def e2e_pipeline(bs, torch, dev, host, seed, args, world):
     three streams with two device buffer pairs, so the copy-in of step i+1 and
     the copy-out of step i-1 overlap the shuffle of step i.
     """
-    steps = max(3, min(20, args.steps // 10))
+    steps = max(3, min(40, args.steps // 5))
     hin = torch.from_numpy(host.view(np.int64)).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
     xs = [torch.empty(N_MAIN, dtype=torch.int64, device=dev) for _ in range(2)]
