@@ -19,19 +19,24 @@ Printed on one JSON line (rank 0):
   e2e          the same metric through the C ABI from pinned host buffers,
                host-to-device and device-to-host copies inside the timed region,
                with the copies alone timed beside it (the host link's floor)
-  cpu_baseline the CPU oracle, as it stands, on a bounded sample of the same
-               workload (the first slots of the same shuffle)
+  cpu_baseline the CPU oracle, as it stands: the whole shuffle once on all
+               host threads, the sequential oracle on its first 2^21 slots,
+               and a sequential Fisher-Yates shuffle of the same keys
   extra        every strategy at n = 2^28 and at the worst-case padding
                n = 2^28 + 12345, the inverse and index outputs, the Sec. 6
                fusion ablation, the Sec. 5 round-count study, the random
                gather bound, the autograd row shuffle, the Monte Carlo and
                Shapley consumers, and the 4096-instance uneven batch
-               (batched launch vs one plain launch per instance)
+               (batched launch vs one plain launch per instance, called
+               from Python and replayed from a CUDA graph)
 
 `--impl reference` times the CPU oracle on this workload instead (bounded
 sample per step) and prints the same line with "impl": "reference".
 Multi-GPU (torchrun): every rank shuffles its own array (independent
-problems, weak scaling) with no collective on the data path.
+problems, weak scaling) with no collective on the data path.  `--split`
+times one shuffle cut by domain range over the ranks instead (strong
+scaling), with each rank's own work at 1, 2, 4 and 8 ranks measured part by
+part at one GPU; `--table1` prints the layout of the paper's Table 1.
 """
 from __future__ import annotations
 
