@@ -104,9 +104,21 @@ def _out_like(x: torch.Tensor, out: torch.Tensor | None) -> torch.Tensor:
     return out
 
 
-def permute(x: torch.Tensor, seed: int, rounds: int = DEFAULT_ROUNDS,
-            out: torch.Tensor | None = None) -> torch.Tensor:
-    """Shuffle x along dim 0: out[j] = x[f(i_j)] (Algorithm 1)."""
+def _along(fn, x: torch.Tensor, seed: int, rounds: int, out, dim: int) -> torch.Tensor:
+    """Apply a dim-0 call along `dim`: the dimension is moved to the front (a
+    copy), its slices are shuffled as rows, and it is moved back (a copy)."""
+    d = dim % x.dim() if x.dim() else 0
+    if d == 0:
+        return fn(x, seed, rounds, out)
+    y = fn(x.movedim(d, 0).contiguous(), seed, rounds, None).movedim(0, d)
+    if out is None:
+        return y.contiguous()
+    if out.shape != x.shape or out.dtype != x.dtype or out.device != x.device:
+        raise ValueError("out must have the input's shape, dtype and device")
+    return out.copy_(y)
+
+
+def _permute0(x: torch.Tensor, seed: int, rounds: int, out) -> torch.Tensor:
     _require_cuda(x, "x")
     x = x.contiguous()
     out = _out_like(x, out)
@@ -114,14 +126,28 @@ def permute(x: torch.Tensor, seed: int, rounds: int = DEFAULT_ROUNDS,
     return out
 
 
-def inverse(y: torch.Tensor, seed: int, rounds: int = DEFAULT_ROUNDS,
-            out: torch.Tensor | None = None) -> torch.Tensor:
-    """Undo :func:`permute`: out[f(i_j)] = y[j]."""
+def permute(x: torch.Tensor, seed: int, rounds: int = DEFAULT_ROUNDS,
+            out: torch.Tensor | None = None, dim: int = 0) -> torch.Tensor:
+    """Shuffle x along `dim` (default 0): out[j] = x[f(i_j)] (Algorithm 1),
+    j and i_j indexing that dimension.  The slices along `dim` are the
+    elements shuffled: 1, 2, 4 or 8 bytes, or a multiple of 16 bytes."""
+    _require_cuda(x, "x")
+    return _along(_permute0, x, seed, rounds, out, dim)
+
+
+def _inverse0(y: torch.Tensor, seed: int, rounds: int, out) -> torch.Tensor:
     _require_cuda(y, "y")
     y = y.contiguous()
     out = _out_like(y, out)
     bshuffle_inverse(y.data_ptr(), out.data_ptr(), y.shape[0], row_bytes(y), seed, rounds, _stream_of(y))
     return out
+
+
+def inverse(y: torch.Tensor, seed: int, rounds: int = DEFAULT_ROUNDS,
+            out: torch.Tensor | None = None, dim: int = 0) -> torch.Tensor:
+    """Undo :func:`permute` along `dim`: out[f(i_j)] = y[j]."""
+    _require_cuda(y, "y")
+    return _along(_inverse0, y, seed, rounds, out, dim)
 
 
 def indices(n: int, seed: int, rounds: int = DEFAULT_ROUNDS, dtype: torch.dtype = torch.int64,
