@@ -733,23 +733,34 @@ def secondary(bs, torch, dev, stream):
     del x, y
 
     # rows: [65536 x 1024] FP32 and BF16 (4 KiB and 2 KiB rows), forward
-    # gather and backward scatter of the autograd row shuffle
-    for dtype, name in ((torch.float32, "fp32"), (torch.bfloat16, "bf16")):
-        rows = torch.randn(*workloads.ROWS_SHAPE, device=dev).to(dtype)
-        res = torch.empty_like(rows)
-        rb = rows.shape[1] * rows.element_size()
-        fwd = lambda: bs.bshuffle_permute(rows.data_ptr(), res.data_ptr(), rows.shape[0], rb, 7, ROUNDS, sptr)  # noqa: E731
-        bwd = lambda: bs.bshuffle_inverse(res.data_ptr(), rows.data_ptr(), rows.shape[0], rb, 7, ROUNDS, sptr)  # noqa: E731
-        for _ in range(3):
-            fwd()
-            bwd()
-        _, tf = timed_launches(fwd, 20, stream, torch)
-        _, tb = timed_launches(bwd, 20, stream, torch)
-        nbytes = 2 * rows.numel() * rows.element_size()
-        out[f"rows_65536x1024_{name}"] = {
-            "forward_ms": tf / 20, "backward_ms": tb / 20,
-            "forward_gbps": nbytes / (tf / 20 * 1e-3) / 1e9, "backward_gbps": nbytes / (tb / 20 * 1e-3) / 1e9}
-        del rows, res
+    # gather and backward scatter of the autograd row shuffle; 65537 rows run
+    # the count and copy kernels instead of the scan-free launch.  A plain
+    # device copy of the same bytes (torch's copy_) is timed the same way:
+    # at 0.1-0.3 GB per call the launch and ramp take a share that the 2 GiB
+    # copy behind the measured peak does not see.
+    for n_rows in (workloads.ROWS_SHAPE[0], workloads.ROWS_SHAPE[0] + 1):
+        for dtype, name in ((torch.float32, "fp32"), (torch.bfloat16, "bf16")):
+            rows = torch.randn(n_rows, workloads.ROWS_SHAPE[1], device=dev).to(dtype)
+            res = torch.empty_like(rows)
+            rb = rows.shape[1] * rows.element_size()
+            fwd = lambda: bs.bshuffle_permute(rows.data_ptr(), res.data_ptr(), rows.shape[0], rb, 7, ROUNDS, sptr)  # noqa: E731
+            bwd = lambda: bs.bshuffle_inverse(res.data_ptr(), rows.data_ptr(), rows.shape[0], rb, 7, ROUNDS, sptr)  # noqa: E731
+            cpy = lambda: res.copy_(rows)  # noqa: E731
+            for _ in range(3):
+                fwd()
+                bwd()
+                cpy()
+            _, tf = timed_launches(fwd, 20, stream, torch)
+            _, tb = timed_launches(bwd, 20, stream, torch)
+            _, tc = timed_launches(cpy, 20, stream, torch)
+            nbytes = 2 * rows.numel() * rows.element_size()
+            out[f"rows_{n_rows}x1024_{name}"] = {
+                "forward_ms": tf / 20, "backward_ms": tb / 20,
+                "forward_gbps": nbytes / (tf / 20 * 1e-3) / 1e9, "backward_gbps": nbytes / (tb / 20 * 1e-3) / 1e9,
+                "forward_frac": nbytes / (tf / 20 * 1e-3) / 1e9 / measured_peaks()[0],
+                "backward_frac": nbytes / (tb / 20 * 1e-3) / 1e9 / measured_peaks()[0],
+                "same_size_copy_ms": tc / 20, "forward_over_copy": (tc / 20) / (tf / 20)}
+            del rows, res
 
     # permutation Monte Carlo: 10,000 shuffles of 100,000 float32 + group-mean difference
     xmc = torch.from_numpy(workloads.mc_samples()).to(dev)

@@ -120,8 +120,12 @@ __global__ void __launch_bounds__(kRowBlock) rows_tile_kernel(const __grid_const
 // before it itself (at most a few thousand L2-resident words).  The copy
 // kernel is a programmatic dependent launch: its CTAs evaluate the bijection
 // and rank their tile while the count kernel runs, and wait for it
-// (griddepcontrol.wait) only before reading the counts.  Counts are stored
-// as tile-status words with tag 0, which no look-back ever accepts.
+// (griddepcontrol.wait) only before reading the counts.  A gather's source
+// rows depend on the tile's ranks alone, so its first loads (two rows of up
+// to 2 KiB, or 4 KiB of a longer row, per warp) are in flight during that
+// wait; all the CTA's threads then read the counts before its tile.  Counts
+// are stored as tile-status words with tag 0, which no look-back ever
+// accepts.
 constexpr uint32_t kRowsSumTiles = 4096;
 
 __device__ __forceinline__ void wait_for_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -154,10 +158,13 @@ __global__ void __launch_bounds__(kRowBlock) rows_copy_kernel(const __grid_const
 {
     constexpr int WARPS = kRowBlock / 32;
     constexpr int TILE_WARPS = ROWS / 32;
+    // a gather's source rows are known before the tile's slots are: its
+    // first loads are issued before the wait for the count kernel
+    constexpr bool kEarlyLoads = MODE == Mode::Gather;
     __shared__ uint32_t s_counts[TILE_WARPS];
     __shared__ uint32_t s_src[ROWS];
-    __shared__ uint32_t s_dst[ROWS];
-    __shared__ uint32_t s_prefix, s_total;
+    __shared__ uint32_t s_part[WARPS];
+    __shared__ uint32_t s_total;
 
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
@@ -175,15 +182,8 @@ __global__ void __launch_bounds__(kRowBlock) rows_copy_kernel(const __grid_const
         mask = __ballot_sync(kFull, keep);
         if (lane == 0) s_counts[warp] = __popc(mask);
     }
-    // the counts of the tiles before this one
-    wait_for_prerequisite_grid();
-    if (warp == 0) {
-        uint32_t sum = 0;
-        for (uint32_t t = lane; t < tile; t += 32u) sum += static_cast<uint32_t>(a.status[t]);
-        sum = __reduce_add_sync(kFull, sum);
-        if (lane == 0) s_prefix = sum;
-    }
     __syncthreads();
+    // ranks within the tile need only this tile's counts
     if (threadIdx.x == 0) {
         uint32_t run = 0;
         for (int w = 0; w < TILE_WARPS; ++w) {
@@ -194,74 +194,107 @@ __global__ void __launch_bounds__(kRowBlock) rows_copy_kernel(const __grid_const
         s_total = run;
     }
     __syncthreads();
-    const uint32_t prefix = s_prefix;
-    if (keep) {
-        const uint32_t local = s_counts[warp] + __popc(mask & dev::lanemask_lt());
-        const uint32_t dst = prefix + local;
-        if (dst >= a.g.n) {
-            dev::record_error(a.ws, dev::kErrDeviceBounds, dst);
-            keep = false;
-        }
-        s_src[local] = keep ? src : 0xffffffffu;
-        s_dst[local] = dst;
-    }
+    if (keep) s_src[s_counts[warp] + __popc(mask & dev::lanemask_lt())] = src;
     __syncthreads();
     const uint32_t count = s_total;
     const uint32_t chunks = a.elem_bytes / 16u;
     const uint4 *in = static_cast<const uint4 *>(a.in);
     uint4 *out = static_cast<uint4 *>(a.out);
-    if (chunks <= 16u * kRowChunkUnroll) {
-        // rows of up to 2 KiB: a warp loads two rows before storing them, so
-        // that each lane keeps up to 8 16-byte loads in flight
-        constexpr int H = kRowChunkUnroll / 2;
+    const bool two_rows = chunks <= 16u * kRowChunkUnroll;
+    constexpr int H = kRowChunkUnroll / 2;
+    // registers of the first step: two rows of up to 2 KiB, or the first
+    // 4 KiB of one longer row
+    uint4 v[2][H];
+    if (kEarlyLoads) {
+        if (two_rows) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t r = warp + static_cast<uint32_t>(h) * WARPS;
+                if (r < count) {
+                    const uint4 *from = in + static_cast<uint64_t>(s_src[r]) * chunks;
+#pragma unroll
+                    for (int u = 0; u < H; ++u) {
+                        const uint32_t c = static_cast<uint32_t>(u) * 32u + lane;
+                        if (c < chunks) v[h][u] = __ldg(from + c);
+                    }
+                }
+            }
+        } else if (warp < count) {
+            const uint4 *from = in + static_cast<uint64_t>(s_src[warp]) * chunks;
+#pragma unroll
+            for (int u = 0; u < kRowChunkUnroll; ++u) {
+                const uint32_t c = static_cast<uint32_t>(u) * 32u + lane;
+                if (c < chunks) v[u / H][u % H] = __ldg(from + c);
+            }
+        }
+    }
+    // the counts of the tiles before this one, summed by every thread
+    wait_for_prerequisite_grid();
+    {
+        uint32_t sum = 0;
+        for (uint32_t t = threadIdx.x; t < tile; t += kRowBlock) sum += static_cast<uint32_t>(a.status[t]);
+        sum = __reduce_add_sync(kFull, sum);
+        if (lane == 0) s_part[warp] = sum;
+    }
+    __syncthreads();
+    uint32_t prefix = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) prefix += s_part[w];
+    if (prefix + count > a.g.n) {  // impossible; kept as a guard, and nothing is written
+        if (threadIdx.x == 0) dev::record_error(a.ws, dev::kErrDeviceBounds, prefix + count - 1u);
+        return;
+    }
+    // row r of the tile (its rank among the kept indices) is slot prefix + r
+    if (two_rows) {
+        // a warp loads two rows before storing them, so that each lane keeps
+        // up to 8 16-byte loads in flight
         for (uint32_t r0 = warp; r0 < count; r0 += 2u * WARPS) {
-            uint4 v[2][H];
             uint64_t to_row[2];
-            bool live[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t r = r0 + static_cast<uint32_t>(h) * WARPS;
-                const uint32_t s = r < count ? s_src[r] : 0xffffffffu;
-                live[h] = s != 0xffffffffu;
-                const uint64_t from_row = MODE == Mode::Gather ? s : s_dst[r < count ? r : 0];
-                to_row[h] = MODE == Mode::Gather ? s_dst[r < count ? r : 0] : s;
+                const uint32_t rr = r < count ? r : r0;
+                const uint64_t from_row = MODE == Mode::Gather ? s_src[rr] : prefix + rr;
+                to_row[h] = MODE == Mode::Gather ? prefix + rr : s_src[rr];
+                if (kEarlyLoads && r0 == warp) continue;  // loaded before the wait
                 const uint4 *from = in + from_row * chunks;
 #pragma unroll
                 for (int u = 0; u < H; ++u) {
                     const uint32_t c = static_cast<uint32_t>(u) * 32u + lane;
-                    if (live[h] && c < chunks) v[h][u] = __ldg(from + c);
+                    if (r < count && c < chunks) v[h][u] = __ldg(from + c);
                 }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
+                const uint32_t r = r0 + static_cast<uint32_t>(h) * WARPS;
                 uint4 *to = out + to_row[h] * chunks;
 #pragma unroll
                 for (int u = 0; u < H; ++u) {
                     const uint32_t c = static_cast<uint32_t>(u) * 32u + lane;
-                    if (live[h] && c < chunks) to[c] = v[h][u];
+                    if (r < count && c < chunks) to[c] = v[h][u];
                 }
             }
         }
         return;
     }
     for (uint32_t r = warp; r < count; r += WARPS) {
-        const uint32_t s = s_src[r];
-        if (s == 0xffffffffu) continue;
-        const uint64_t from_row = MODE == Mode::Gather ? s : s_dst[r];
-        const uint64_t to_row = MODE == Mode::Gather ? s_dst[r] : s;
+        const uint64_t from_row = MODE == Mode::Gather ? s_src[r] : prefix + r;
+        const uint64_t to_row = MODE == Mode::Gather ? prefix + r : s_src[r];
         const uint4 *from = in + from_row * chunks;
         uint4 *to = out + to_row * chunks;
         for (uint32_t c0 = 0; c0 < chunks; c0 += 32u * kRowChunkUnroll) {
-            uint4 v[kRowChunkUnroll];
+            const bool preloaded = kEarlyLoads && r == warp && c0 == 0u;
+            if (!preloaded) {
 #pragma unroll
-            for (int u = 0; u < kRowChunkUnroll; ++u) {
-                const uint32_t c = c0 + static_cast<uint32_t>(u) * 32u + lane;
-                if (c < chunks) v[u] = __ldg(from + c);
+                for (int u = 0; u < kRowChunkUnroll; ++u) {
+                    const uint32_t c = c0 + static_cast<uint32_t>(u) * 32u + lane;
+                    if (c < chunks) v[u / H][u % H] = __ldg(from + c);
+                }
             }
 #pragma unroll
             for (int u = 0; u < kRowChunkUnroll; ++u) {
                 const uint32_t c = c0 + static_cast<uint32_t>(u) * 32u + lane;
-                if (c < chunks) to[c] = v[u];
+                if (c < chunks) to[c] = v[u / H][u % H];
             }
         }
     }

@@ -21,9 +21,13 @@ def bs():
     return paper_2106_06161_gb300
 
 
+@pytest.mark.parametrize("extra_row", [0, 1])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_row_shuffle_forward_backward(bs, dtype):
+def test_row_shuffle_forward_backward(bs, dtype, extra_row):
+    # 65536 rows: the scan-free launch; 65537 rows (domain 2^17, about half
+    # of the images dropped): the count kernel and the copy kernel
     rows, cols = workloads.ROWS_SHAPE
+    rows += extra_row
     seed = workloads.ROWS_SEED
     host = torch.from_numpy(workloads.normal_rows(rows, cols)).to(dtype)
     x = host.cuda().requires_grad_(True)
@@ -57,8 +61,10 @@ def test_gradcheck_fp64(bs):
 
 
 def test_row_widths_and_inverse(bs):
+    # rows of 16 B to 4,112 B; 2,080 and 4,112 B rows are longer than 2 KiB
+    # and not a whole number of 4 KiB blocks
     for cols, dt in ((2, torch.float64), (12, torch.float32), (1024, torch.float32), (6, torch.int64),
-                     (4, torch.int16)):
+                     (4, torch.int16), (520, torch.float32), (1028, torch.float32)):
         for n in (1, 17, 300, 5000):
             x = torch.randn(n, cols, dtype=torch.float64).to(dt).cuda() if dt.is_floating_point else \
                 torch.randint(-9, 9, (n, cols), dtype=dt).cuda()
