@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import golden
 
 M0 = 0xD2B74407B1CE6E93  # the Philox constant printed in Listing 1
 MASK64 = (1 << 64) - 1
@@ -28,10 +29,12 @@ def test_domain_bits_is_nearest_power_of_two_with_floor_4():
 
 
 def test_round_keys_are_splitmix64_outputs():
-    # First three outputs of the published SplitMix64 generator from state 0:
-    # 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F; the round
-    # keys are their low 32 bits (reading R3).
-    keys = oracle.round_keys(0, 3)
+    # The first three outputs of the published SplitMix64 generator from
+    # state 0 (tests/golden); the round keys are their low 32 bits.
+    g = golden.load("splitmix64_state0.txt")
+    outputs = [int(v, 16) for v in g["outputs"].split()]
+    keys = oracle.round_keys(int(g["seed"]), len(outputs))
+    assert [int(k) for k in keys] == [v & 0xFFFFFFFF for v in outputs]
     assert [int(k) for k in keys] == [0x7B1DCDAF, 0xA1B965F4, 0x8009454F]
     # keys depend on the seed only, not on n, and a prefix is stable
     assert np.array_equal(oracle.round_keys(7, 24)[:10], oracle.round_keys(7, 10))

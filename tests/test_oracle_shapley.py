@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from oracle.shapley import shapley_shubik
+from tests import golden
 
 
 def _by_enumeration(weights, quota):
@@ -44,13 +45,14 @@ def test_small_textbook_game():
 
 
 def test_security_council_game():
-    # UN Security Council as analysed by Shapley and Shubik (1954, American
-    # Political Science Review 48): five permanent members of weight 7, ten
-    # members of weight 1, quota 39.  Each permanent member has 421/2145,
-    # each other member 4/2145.
-    phi = shapley_shubik([7] * 5 + [1] * 10, 39)
-    assert phi[:5] == [Fraction(421, 2145)] * 5
-    assert phi[5:] == [Fraction(4, 2145)] * 10
+    # The UN Security Council as analysed by Shapley and Shubik (1954), values
+    # stored in tests/golden.
+    g = golden.load("shapley_shubik_security_council.txt")
+    weights = [int(v) for v in g["weights"].split()]
+    want = [Fraction(v) for v in g["values"].split()]
+    phi = shapley_shubik(weights, int(g["quota"]))
+    assert phi == want
+    assert phi[:5] == [Fraction(421, 2145)] * 5 and phi[5:] == [Fraction(4, 2145)] * 10
 
 
 def test_exact_value_axioms():

@@ -9,6 +9,7 @@ import pytest
 import oracle
 import workloads
 from oracle import stats
+from tests import golden
 
 
 def _brute_force_indices(n, seed, rounds, k):
@@ -87,13 +88,14 @@ def test_literal_domain_override():
 
 
 def test_sec2_worked_example_of_the_convention():
-    # Sec. 2: sigma = (0 3 1 2) reorders (x0, x1, x2, x3) into (x0, x2, x3, x1).
-    # Slot j of a shuffle output holds element idx[j], so sigma = idx^-1.
-    sigma = np.array([[0, 3, 1, 2]])
+    # Sec. 2's example of one-line notation (tests/golden): slot j of a
+    # shuffle output holds element idx[j], so sigma = idx^-1.
+    g = golden.load("sec2_one_line_notation.txt")
+    sigma = np.array([[int(v) for v in g["sigma"].split()]])
+    items = np.array(g["items"].split())
     idx = np.argsort(sigma, axis=1)
     assert idx.tolist() == [[0, 2, 3, 1]]
-    items = np.array(["x0", "x1", "x2", "x3"])
-    assert items[idx[0]].tolist() == ["x0", "x2", "x3", "x1"]
+    assert items[idx[0]].tolist() == g["reordered"].split()
     assert stats.ranks_from_indices(idx).tolist() == sigma.tolist()
 
 

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from oracle import stats
+from tests import golden
 
 
 def _ndis_brute(s, t):
@@ -55,12 +56,15 @@ def test_chi2_harness_controls():
 
 
 def test_chi2_n5_paper_round_count():
-    # Sec. 5: at n = 5 with 100,000 permutations, fewer than 20 rounds are
-    # unlikely to be uniform, while 24 rounds pass.
-    idx24 = oracle.sample_permutations(5, 100_000, seed0=0, rounds=24)
-    chi24, _, crit = stats.chi2_uniform(stats.ranks_from_indices(idx24))
+    # Sec. 5 (tests/golden): at n = 5 with 100,000 permutations, fewer than
+    # 20 rounds are unlikely to be uniform, while 24 rounds pass.
+    g = golden.load("sec5_chi2_n5.txt")
+    n, perms = int(g["n"]), int(g["permutations"])
+    idx24 = oracle.sample_permutations(n, perms, seed0=0, rounds=int(g["passing_rounds"]))
+    chi24, dof, crit = stats.chi2_uniform(stats.ranks_from_indices(idx24))
+    assert dof == int(g["dof"])
     assert chi24 < crit, chi24
-    idx16 = oracle.sample_permutations(5, 100_000, seed0=0, rounds=16)
+    idx16 = oracle.sample_permutations(n, perms, seed0=0, rounds=int(g["failing_rounds"]))
     chi16, _, _ = stats.chi2_uniform(stats.ranks_from_indices(idx16))
     assert chi16 > crit, chi16
 
@@ -103,9 +107,11 @@ def test_mmd_detects_too_few_rounds():
 
 
 def test_chi2_lcg_fails_in_the_paper_region():
-    # Sec. 5: the LCG bijective function gives a chi-squared statistic in the
-    # region of 500,000 at n = 5 (100,000 permutations).
-    perms = oracle.sample_permutations_lcg(5, 100_000, 0)
+    # Sec. 5 (tests/golden): the LCG bijective function scores about 500,000
+    # at n = 5 (100,000 permutations).
+    g = golden.load("sec5_chi2_n5.txt")
+    lo, hi = (int(v) for v in g["lcg_chi2_range"].split())
+    perms = oracle.sample_permutations_lcg(int(g["n"]), int(g["permutations"]), 0)
     chi, _, crit = stats.chi2_uniform(stats.ranks_from_indices(perms))
-    assert 300_000 < chi < 800_000, chi
+    assert lo < chi < hi, chi
     assert chi > 1000 * crit
