@@ -263,6 +263,22 @@ def timed_launches(fn, steps, stream, torch):
     return per, region0.elapsed_time(region1)
 
 
+def timed_region(fn, steps, stream, torch):
+    """Milliseconds per launch of `steps` back-to-back launches, one pair of
+    CUDA events around them all (no event between launches: for kernels of
+    tens of microseconds an event pair per launch adds a gap of the same
+    order as the launch ramp)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def traffic_for(kernel: str, fingerprint: str):
     """DRAM bytes per launch from the committed ncu record, if the kernel is unchanged."""
     if not os.path.exists(TRAFFIC_FILE):
@@ -734,9 +750,10 @@ def secondary(bs, torch, dev, stream):
 
     # rows: [65536 x 1024] FP32 and BF16 (4 KiB and 2 KiB rows), forward
     # gather and backward scatter of the autograd row shuffle; 65537 rows run
-    # the count and copy kernels instead of the scan-free launch.  A plain
-    # device copy of the same bytes (torch's copy_) is timed the same way:
-    # at 0.1-0.3 GB per call the launch and ramp take a share that the 2 GiB
+    # the count and copy kernels instead of the scan-free launch.  Each is
+    # timed over 50 back-to-back calls between one pair of events, and a
+    # plain device copy of the same bytes (torch's copy_) the same way: at
+    # 0.1-0.3 GB per call the launch and ramp take a share that the 2 GiB
     # copy behind the measured peak does not see.
     for n_rows in (workloads.ROWS_SHAPE[0], workloads.ROWS_SHAPE[0] + 1):
         for dtype, name in ((torch.float32, "fp32"), (torch.bfloat16, "bf16")):
@@ -750,16 +767,16 @@ def secondary(bs, torch, dev, stream):
                 fwd()
                 bwd()
                 cpy()
-            _, tf = timed_launches(fwd, 20, stream, torch)
-            _, tb = timed_launches(bwd, 20, stream, torch)
-            _, tc = timed_launches(cpy, 20, stream, torch)
+            tf = timed_region(fwd, 50, stream, torch)
+            tb = timed_region(bwd, 50, stream, torch)
+            tc = timed_region(cpy, 50, stream, torch)
             nbytes = 2 * rows.numel() * rows.element_size()
             out[f"rows_{n_rows}x1024_{name}"] = {
-                "forward_ms": tf / 20, "backward_ms": tb / 20,
-                "forward_gbps": nbytes / (tf / 20 * 1e-3) / 1e9, "backward_gbps": nbytes / (tb / 20 * 1e-3) / 1e9,
-                "forward_frac": nbytes / (tf / 20 * 1e-3) / 1e9 / measured_peaks()[0],
-                "backward_frac": nbytes / (tb / 20 * 1e-3) / 1e9 / measured_peaks()[0],
-                "same_size_copy_ms": tc / 20, "forward_over_copy": (tc / 20) / (tf / 20)}
+                "forward_ms": tf, "backward_ms": tb,
+                "forward_gbps": nbytes / (tf * 1e-3) / 1e9, "backward_gbps": nbytes / (tb * 1e-3) / 1e9,
+                "forward_frac": nbytes / (tf * 1e-3) / 1e9 / measured_peaks()[0],
+                "backward_frac": nbytes / (tb * 1e-3) / 1e9 / measured_peaks()[0],
+                "same_size_copy_ms": tc, "forward_over_copy": tc / tf}
             del rows, res
 
     # permutation Monte Carlo: 10,000 shuffles of 100,000 float32 + group-mean difference
