@@ -50,7 +50,10 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        # BSHUFFLE_ORACLE_LIB names another build of this source to load
+        # instead: the test that plants mistakes in the oracle (each in a
+        # temporary copy of bshuffle_oracle.c) runs the pins against it.
+        lib = ctypes.CDLL(os.environ.get("BSHUFFLE_ORACLE_LIB") or build())
         u32, u64, p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
         sig = {
             "oracle_domain_bits": (u32, [u64]),
