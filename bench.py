@@ -77,6 +77,8 @@ def parse():
                    help="how bshuffle_permute moves data (identical output)")
     p.add_argument("--profile-batched", type=int, default=0,
                    help="only run warmup + steps batched launches over this many instances (for ncu)")
+    p.add_argument("--profile-rows", type=int, default=0,
+                   help="only run warmup + steps forward row shuffles of a [this many x 1024] BF16 matrix (for ncu)")
     p.add_argument("--profile-n", type=int, default=0,
                    help="only run warmup + steps launches of the uint64 shuffle at this n (for ncu)")
     p.add_argument("--table1", action="store_true",
@@ -911,6 +913,27 @@ def profile_batched(args):
     print(json.dumps({"profile_batched": len(sizes), "elements": int(sizes.sum()), "launch_ms": per}))
 
 
+def profile_rows(args):
+    """warmup + steps forward row shuffles of a [--profile-rows x 1024] BF16 matrix."""
+    import torch
+    from paper_2106_06161_gb300 import build as bsbuild
+    bsbuild.build()
+    import paper_2106_06161_gb300 as bs
+    n_rows, cols = args.profile_rows, workloads.ROWS_SHAPE[1]
+    rows = torch.from_numpy(workloads.normal_rows(n_rows, cols)).to(torch.bfloat16).cuda()
+    res = torch.empty_like(rows)
+    sptr = torch.cuda.current_stream().cuda_stream
+    f = lambda: bs.bshuffle_permute(rows.data_ptr(), res.data_ptr(), n_rows, cols * 2,  # noqa: E731
+                                    workloads.ROWS_SEED, ROUNDS, sptr)
+    for _ in range(args.warmup):
+        f()
+    ms = timed_region(f, args.steps, torch.cuda.current_stream(), torch)
+    if bs.get_error() != 0:
+        raise SystemExit("device error")
+    print(json.dumps({"profile_rows": n_rows, "row_bytes": cols * 2, "launch_ms": ms,
+                      "gbps": 2 * n_rows * cols * 2 / (ms * 1e-3) / 1e9}))
+
+
 TABLE1_W = (8, 11, 14, 17, 20, 23, 26, 29)
 
 
@@ -1134,6 +1157,8 @@ def main():
         table1(args)
     elif args.profile_batched:
         profile_batched(args)
+    elif args.profile_rows:
+        profile_rows(args)
     elif args.profile_n:
         profile_case(args)
     elif args.impl == "reference":

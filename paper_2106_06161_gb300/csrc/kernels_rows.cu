@@ -115,8 +115,7 @@ __global__ void __launch_bounds__(kRowBlock) rows_tile_kernel(const __grid_const
 // ------------------------------------------------------------------ two-kernel form
 //
 // For up to kRowsSumTiles tiles the inter-tile prefix needs no chain: the
-// count kernel writes every tile's kept count (one small CTA per tile, no
-// data read), and each CTA of the copy kernel adds the counts of the tiles
+// count kernel writes every tile's kept count (no data read), and each CTA of the copy kernel adds the counts of the tiles
 // before it itself (at most a few thousand L2-resident words).  The copy
 // kernel is a programmatic dependent launch: its CTAs evaluate the bijection
 // and rank their tile while the count kernel runs, and wait for it
@@ -131,13 +130,21 @@ constexpr uint32_t kRowsSumTiles = 4096;
 __device__ __forceinline__ void wait_for_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_dependent_grid() { asm volatile("griddepcontrol.launch_dependents;"); }
 
+// The count kernel's CTAs: 1,024 threads, one domain index each, counting
+// 1024 / ROWS tiles.  A [65537 x 1024] shuffle (domain 2^17) needs 128 of
+// them, one resident wave, where one small CTA per tile (1,024 CTAs) took
+// 4.5 us, mostly to dispatch.
+constexpr int kCountBlock = 1024;
+
 template <bool ODD, int ROWS>
-__global__ void __launch_bounds__(ROWS) rows_count_kernel(const __grid_constant__ TileArgs a)
+__global__ void __launch_bounds__(kCountBlock) rows_count_kernel(const __grid_constant__ TileArgs a)
 {
     allow_dependent_grid();
-    __shared__ uint32_t s_count[ROWS / 32];
+    constexpr int WARPS_PER_TILE = ROWS / 32;
+    constexpr int TILES = kCountBlock / ROWS;
+    __shared__ uint32_t s_count[kCountBlock / 32];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t i = blockIdx.x * static_cast<uint32_t>(ROWS) + threadIdx.x;
+    const uint32_t i = blockIdx.x * static_cast<uint32_t>(kCountBlock) + threadIdx.x;
     uint32_t left[1] = {i >> a.g.R};
     uint32_t right[1] = {i & a.g.rmask};
     dev::cipher_items<ODD, 1>(left, right, a.keys, a.rounds, a.g);
@@ -146,10 +153,12 @@ __global__ void __launch_bounds__(ROWS) rows_count_kernel(const __grid_constant_
     const uint32_t c = __popc(__ballot_sync(kFull, keep));
     if (lane == 0) s_count[warp] = c;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < static_cast<uint32_t>(TILES)) {
+        const uint32_t tile = blockIdx.x * static_cast<uint32_t>(TILES) + threadIdx.x;
         uint32_t total = 0;
-        for (int w = 0; w < ROWS / 32; ++w) total += s_count[w];
-        a.status[blockIdx.x] = total;  // tag 0: never read as a published status
+#pragma unroll
+        for (int w = 0; w < WARPS_PER_TILE; ++w) total += s_count[threadIdx.x * WARPS_PER_TILE + w];
+        if (tile < a.num_tiles) a.status[tile] = total;  // tag 0: never read as a published status
     }
 }
 
@@ -303,7 +312,9 @@ __global__ void __launch_bounds__(kRowBlock) rows_copy_kernel(const __grid_const
 template <Mode MODE, bool ODD, int ROWS>
 cudaError_t launch_two_kernel(const TileArgs &a, cudaStream_t stream)
 {
-    rows_count_kernel<ODD, ROWS><<<a.num_tiles, ROWS, 0, stream>>>(a);
+    constexpr uint32_t tiles_per_count_cta = kCountBlock / ROWS;
+    rows_count_kernel<ODD, ROWS><<<(a.num_tiles + tiles_per_count_cta - 1) / tiles_per_count_cta, kCountBlock, 0,
+                                   stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
