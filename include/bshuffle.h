@@ -33,7 +33,7 @@
  *             (BSHUFFLE_DEFAULT_ROUNDS); 0 rounds is the identity bijection.
  * Keys.       key[r] = low 32 bits of the r-th output of SplitMix64 seeded with
  *             `seed` (Steele, Lea, Flood 2014).  The paper leaves the key
- *             schedule open ("key[i]", Listing 1; Sec. 7).
+ *             schedule open (one key per round in Listing 1; Sec. 7).
  * Sizes.      0 <= n <= BSHUFFLE_MAX_N.  n = 0 is a successful no-op.
  * Elements.   elem_bytes is 1, 2, 4, 8, or a positive multiple of 16 (rows of
  *             a matrix, moved whole).  Elements are raw bytes: the library

@@ -23,13 +23,15 @@
  *   R2  the power-of-two domain has k = max(ceil(log2 n), 4) bits: with fewer
  *       than 4 bits the left half has at most one bit, the multiply is linear
  *       over GF(2) and the cipher can only reach 2^k affine permutations
- *       (Sec. 4 says "nearest power of two"; the 4-bit floor is the reading
- *       under which the Sec. 5 chi-squared result at n = 5 is reachable).
+ *       (Sec. 4 takes the power of two closest above n; the 4-bit floor is
+ *       the reading under which the Sec. 5 chi-squared result at n = 5 is
+ *       reachable).
  *       The *_k entry points take k explicitly so the literal rule stays
  *       testable.
  *   R3  the round keys are the low 32 bits of successive SplitMix64 outputs
  *       (Steele, Lea, Flood, OOPSLA 2014) started from the 64-bit seed; the
- *       paper only says "key[i]" and never gives a seed-to-key schedule.
+ *       paper indexes one key per round and never gives a seed-to-key
+ *       schedule.
  *   R4  an image b is kept when b < n and dropped when b >= n (Algorithm 1).
  *   R5  output convention: slot j receives X[f(i_j)], where i_j is the j-th
  *       domain index, in increasing order, whose image is kept (Algorithm 1
