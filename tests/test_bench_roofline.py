@@ -1,4 +1,4 @@
-"""The roofline arithmetic of bench.py on CPU: algorithmic bytes and
+"""The roofline arithmetic and timing helpers of bench.py on CPU: algorithmic bytes and
 evaluations per launch, the dominant kernel of a step, the measured peak, and
 the DRAM traffic taken from the committed ncu record only while the kernel's
 source fingerprint matches."""
@@ -97,3 +97,50 @@ def test_kernel_fingerprint_covers_headers(tmp_path, monkeypatch):
     assert bsbuild.kernel_fingerprint("kernels_staged.cu") == fp
     (csrc / "bshuffle_internal.h").write_text((csrc / "bshuffle_internal.h").read_text() + "\n// a header\n")
     assert bsbuild.kernel_fingerprint("kernels_staged.cu") != fp
+
+
+class _FakeEvent:
+    """Stands in for torch.cuda.Event: a clock that the fake launches advance."""
+    clock = [0.0]
+
+    def __init__(self, enable_timing=True):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = _FakeEvent.clock[0]
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+class _FakeTorch:
+    class cuda:  # noqa: N801 - mirrors torch.cuda
+        Event = _FakeEvent
+
+        @staticmethod
+        def synchronize():
+            pass
+
+
+def test_timed_region_is_time_per_call_between_one_event_pair():
+    _FakeEvent.clock[0] = 0.0
+    calls = []
+
+    def launch():
+        calls.append(1)
+        _FakeEvent.clock[0] += 0.046     # ms of device time per call
+
+    ms = bench.timed_region(launch, 50, None, _FakeTorch)
+    assert len(calls) == 50
+    assert ms == pytest.approx(0.046)
+
+
+def test_timed_launches_reports_each_call_and_the_region():
+    _FakeEvent.clock[0] = 0.0
+
+    def launch():
+        _FakeEvent.clock[0] += 3.7
+
+    per, region = bench.timed_launches(launch, 4, None, _FakeTorch)
+    assert per == pytest.approx([3.7] * 4)
+    assert region == pytest.approx(4 * 3.7)
